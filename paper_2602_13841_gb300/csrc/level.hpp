@@ -1,0 +1,42 @@
+// Host-side description of one level of the hp space-time hierarchy and the operator launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "refdata.hpp"
+
+namespace stmg {
+
+struct Level {
+  int d = 2, n = 0, r = 1, k = 0;
+  int N1 = 0, npc = 0;
+  int64_t nnodes = 0, Nv = 0, Np = 0, Nst = 0;
+  LevelTables tabs{};
+  double* verts64 = nullptr;          // device, (n+1)^d * d
+  float* verts32 = nullptr;
+  ColorInfo colors[8]{};
+  int* bcells[8]{};                   // device lists of boundary cells per colour
+  int nbcells[8]{};
+  int ncolors = 0;
+};
+
+struct Problem {
+  double nu, tau, gamma1, gamma2;
+  int bconv, problem;
+};
+
+template <typename T>
+LevelArgs<T> level_args(const Level& lv, const Problem& pb, double t0);
+
+// y (+)= operator(x): J(state) x when res == false, R(x; vprev) when res == true.  y is zeroed
+// first.  Enqueued on `stream`; returns the first CUDA error.
+template <typename T>
+cudaError_t launch_operator(const Level& lv, const Problem& pb, bool res, double t0, const T* x,
+                            const T* state, const T* vprev, T* y, cudaStream_t stream);
+
+cudaError_t launch_initial_condition(const Level& lv, const Problem& pb, double* V0, cudaStream_t s);
+
+}  // namespace stmg

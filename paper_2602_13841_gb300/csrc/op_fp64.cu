@@ -1,0 +1,51 @@
+// FP64 operator kernels: Jacobian apply and residual (outer Newton-Krylov level), and the
+// nodal interpolation of the initial velocity.
+#include <type_traits>
+#include "op_launch.cuh"
+
+namespace stmg {
+
+template <>
+cudaError_t launch_operator<double>(const Level& lv, const Problem& pb, bool res, double t0,
+                                    const double* x, const double* state, const double* vprev,
+                                    double* y, cudaStream_t s) {
+  if (res) return launch_any<double, true>(lv, pb, t0, x, state, vprev, y, s);
+  return launch_any<double, false>(lv, pb, t0, x, state, vprev, y, s);
+}
+
+// v_{0,h}: v0 evaluated at the mapped Gauss-Lobatto nodes (one thread per global node).
+template <int D>
+__global__ void k_initial(LevelArgs<double> L, Tab<double> tb, int r1, double* V0) {
+  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gi >= L.nnodes) return;
+  int gm[3] = {0, 0, 0};
+  int64_t rem = gi;
+  for (int l = 0; l < D; ++l) { gm[l] = (int)(rem % L.N1); rem /= L.N1; }
+  int cc[3] = {0, 0, 0};
+  double xh[3];
+  for (int l = 0; l < D; ++l) {
+    cc[l] = gm[l] / r1; if (cc[l] >= L.n) cc[l] = L.n - 1;
+    xh[l] = tb.gll[gm[l] - cc[l] * r1];
+  }
+  double corner[8][3];
+  for (int c = 0; c < (1 << D); ++c) {
+    int64_t v = 0, s = 1;
+    for (int l = 0; l < D; ++l) { v += (int64_t)(cc[l] + ((c >> l) & 1)) * s; s *= (L.n + 1); }
+    for (int i = 0; i < D; ++i) corner[c][i] = L.verts[v * D + i];
+  }
+  double J[3][3], x[3], v0[3];
+  map_jacobian<double, D>(corner, xh, J, x);
+  problem_v0<D>(L.problem, x, L.nu, v0);
+  for (int c = 0; c < D; ++c) V0[c * L.nnodes + gi] = v0[c];
+}
+
+cudaError_t launch_initial_condition(const Level& lv, const Problem& pb, double* V0, cudaStream_t s) {
+  LevelArgs<double> L = level_args<double>(lv, pb, 0.0);
+  Tab<double> tb = make_tab<double>(lv.tabs, pb.tau);
+  int64_t blocks = (lv.nnodes + 255) / 256;
+  if (lv.d == 2) k_initial<2><<<(unsigned)blocks, 256, 0, s>>>(L, tb, lv.r + 1, V0);
+  else k_initial<3><<<(unsigned)blocks, 256, 0, s>>>(L, tb, lv.r + 1, V0);
+  return cudaGetLastError();
+}
+
+}  // namespace stmg

@@ -1,0 +1,251 @@
+// C ABI entry points: handle life cycle, hierarchy construction, operator apply, residual.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/stmg.h"
+#include "handle.hpp"
+
+using namespace stmg;
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+namespace stmg {
+
+int height(int x) { int h = 0; while (x > 1) { x /= 2; ++h; } return h; }
+
+stmg_status Handle::fail(stmg_status s, const std::string& msg) {
+  err = msg;
+  return s;
+}
+
+void* Handle::dalloc(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); throw std::bad_alloc(); }
+  allocs.push_back(p);
+  return p;
+}
+
+Handle::~Handle() {
+  for (void* p : allocs) cudaFree(p);
+}
+
+static void build_level(Handle* h, Level& lv, const std::vector<double>& verts) {
+  lv.N1 = (lv.r + 1) * lv.n + 1;
+  lv.nnodes = 1;
+  for (int l = 0; l < lv.d; ++l) lv.nnodes *= lv.N1;
+  lv.tabs.build(lv.d, lv.r, lv.k);
+  lv.npc = lv.tabs.npc;
+  lv.Nv = lv.d * lv.nnodes;
+  int64_t ncells = 1;
+  for (int l = 0; l < lv.d; ++l) ncells *= lv.n;
+  lv.Np = ncells * lv.npc;
+  lv.Nst = (int64_t)(lv.k + 1) * (lv.Nv + lv.Np);
+  lv.verts64 = (double*)h->dalloc(verts.size() * sizeof(double));
+  lv.verts32 = (float*)h->dalloc(verts.size() * sizeof(float));
+  std::vector<float> v32(verts.begin(), verts.end());
+  cudaMemcpy(lv.verts64, verts.data(), verts.size() * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(lv.verts32, v32.data(), v32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  lv.ncolors = 1 << lv.d;
+  for (int c = 0; c < lv.ncolors; ++c) {
+    ColorInfo& ci = lv.colors[c];
+    ci.color = c;
+    ci.count = 1;
+    for (int l = 0; l < 3; ++l) ci.cnt[l] = 1;
+    for (int l = 0; l < lv.d; ++l) {
+      int bit = (c >> l) & 1;
+      ci.cnt[l] = (lv.n - bit + 1) / 2;
+      ci.count *= ci.cnt[l];
+    }
+    std::vector<int> bc;
+    for (int64_t cell = 0; cell < ncells; ++cell) {
+      int64_t rem = cell;
+      bool bnd = false, match = true;
+      for (int l = 0; l < lv.d; ++l) {
+        int x = (int)(rem % lv.n); rem /= lv.n;
+        if (x == 0 || x == lv.n - 1) bnd = true;
+        if ((x & 1) != ((c >> l) & 1)) match = false;
+      }
+      if (bnd && match) bc.push_back((int)cell);
+    }
+    lv.nbcells[c] = (int)bc.size();
+    lv.bcells[c] = (int*)h->dalloc(bc.size() * sizeof(int));
+    if (!bc.empty()) cudaMemcpy(lv.bcells[c], bc.data(), bc.size() * sizeof(int), cudaMemcpyHostToDevice);
+  }
+}
+
+static std::vector<double> coarsen_vertices(const std::vector<double>& v, int d, int n) {
+  int nc = n / 2;
+  std::vector<double> out;
+  int M = n + 1, Mc = nc + 1;
+  int64_t tot = 1;
+  for (int l = 0; l < d; ++l) tot *= Mc;
+  out.resize(tot * d);
+  for (int64_t i = 0; i < tot; ++i) {
+    int64_t rem = i, src = 0, s = 1;
+    for (int l = 0; l < d; ++l) { int x = (int)(rem % Mc); rem /= Mc; src += (int64_t)(2 * x) * s; s *= M; }
+    for (int j = 0; j < d; ++j) out[i * d + j] = v[src * d + j];
+  }
+  return out;
+}
+
+}  // namespace stmg
+
+extern "C" {
+
+void stmg_params_default(stmg_params* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->dim = 2; p->n_cells_1d = 8; p->r = 1; p->k = 1;
+  p->nu = 1e-2; p->tau = 0.1; p->gamma1 = 10.0; p->gamma2 = 10.0;
+  p->problem = STMG_TG2D; p->bconv = 1; p->n_levels_h = -1;
+  p->precond_precision = STMG_FP32;
+  p->nu1 = 1; p->nu2 = 1; p->omega = 0.7;
+  p->newton_rtol = 1e-8; p->newton_atol = 1e-12; p->newton_maxit = 20;
+  p->ew_eta0 = 0.4; p->ew_c = 0.5; p->ew_theta = 1.5; p->ew_min = 1e-3; p->ew_max = 0.8;
+  p->ls_lambda0 = 1.0; p->ls_c = 1e-4; p->ls_tau = 0.5; p->ls_alpha_min = 1e-3;
+  p->ls_maxbt = 5; p->ls_window = 5;
+  p->gmres_restart = 30; p->gmres_maxit = 50;
+  p->rebuild_thetaN = 0.5; p->rebuild_thetaL = 2.0; p->rebuild_kappa_abs = 20;
+  p->stag_s = 3; p->stag_theta = 0.95;
+}
+
+stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_stream stream,
+                        stmg_handle** out) {
+  if (!p || !out) return STMG_ERR_ARG;
+  *out = nullptr;
+  if (p->dim < 2 || p->dim > 3 || p->r < 1 || p->r > 3 || p->k < 0 || p->k > 2 ||
+      p->n_cells_1d < 1 || p->n_cells_1d > 4096 || !(p->tau > 0) || !(p->nu > 0))
+    return STMG_ERR_ARG;
+  auto h = std::make_unique<Handle>();
+  h->prm = *p;
+  h->stream = (cudaStream_t)stream;
+  h->pb = Problem{p->nu, p->tau, p->gamma1, p->gamma2, p->bconv, p->problem};
+  const int d = p->dim, n = p->n_cells_1d;
+  std::vector<double> verts;
+  int64_t nv = 1;
+  for (int l = 0; l < d; ++l) nv *= (n + 1);
+  if (nv * d > ((int64_t)1 << 31)) return STMG_ERR_ARG;
+  verts.resize(nv * d);
+  if (vertices) {
+    std::memcpy(verts.data(), vertices, verts.size() * sizeof(double));
+  } else {
+    for (int64_t i = 0; i < nv; ++i) {
+      int64_t rem = i;
+      for (int l = 0; l < d; ++l) { verts[i * d + l] = (double)(rem % (n + 1)) / n; rem /= (n + 1); }
+    }
+  }
+  // hierarchy: p-coarsening first (taller of the r / k hierarchies alone until the heights
+  // match, then both), then h-coarsening of the space mesh (Sec. 4.2, "cycle and coarsening order")
+  try {
+    int r = p->r, k = p->k;
+    std::vector<std::pair<int, int>> pk{{r, k}};
+    while (height(r) > 0 || height(k) > 0) {
+      if (height(r) > height(k)) r /= 2;
+      else if (height(k) > height(r)) k /= 2;
+      else { r /= 2; k /= 2; }
+      pk.push_back({r, k});
+    }
+    for (auto& rk : pk) {
+      Level lv; lv.d = d; lv.n = n; lv.r = rk.first; lv.k = rk.second;
+      build_level(h.get(), lv, verts);
+      h->levels.push_back(lv);
+    }
+    int nn = n, hl = 0;
+    std::vector<double> cv = verts;
+    while (nn % 2 == 0 && nn / 2 >= 2 && (p->n_levels_h < 0 || hl < p->n_levels_h)) {
+      cv = coarsen_vertices(cv, d, nn);
+      nn /= 2; ++hl;
+      Level lv; lv.d = d; lv.n = nn; lv.r = r; lv.k = k;
+      build_level(h.get(), lv, cv);
+      h->levels.push_back(lv);
+    }
+  } catch (const std::bad_alloc&) {
+    return STMG_ERR_OOM;
+  } catch (const std::exception&) {
+    return STMG_ERR_ARG;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); return STMG_ERR_CUDA; }
+  *out = reinterpret_cast<stmg_handle*>(h.release());
+  return STMG_OK;
+}
+
+void stmg_destroy(stmg_handle* hh) {
+  delete reinterpret_cast<Handle*>(hh);
+}
+
+const char* stmg_last_error(const stmg_handle* hh) {
+  if (!hh) return "null handle";
+  return reinterpret_cast<const Handle*>(hh)->err.c_str();
+}
+
+stmg_status stmg_num_levels(const stmg_handle* hh, int* n_levels) {
+  if (!hh || !n_levels) return STMG_ERR_ARG;
+  *n_levels = (int)reinterpret_cast<const Handle*>(hh)->levels.size();
+  return STMG_OK;
+}
+
+stmg_status stmg_level_info(const stmg_handle* hh, int level, int* n_cells_1d, int* r, int* k,
+                            int64_t* n_v, int64_t* n_p, int64_t* n_st) {
+  if (!hh) return STMG_ERR_ARG;
+  const Handle* h = reinterpret_cast<const Handle*>(hh);
+  if (level < 0 || level >= (int)h->levels.size()) return STMG_ERR_ARG;
+  const Level& lv = h->levels[level];
+  if (n_cells_1d) *n_cells_1d = lv.n;
+  if (r) *r = lv.r;
+  if (k) *k = lv.k;
+  if (n_v) *n_v = lv.Nv;
+  if (n_p) *n_p = lv.Np;
+  if (n_st) *n_st = lv.Nst;
+  return STMG_OK;
+}
+
+stmg_status stmg_apply(stmg_handle* hh, int level, int precision, const void* U_state,
+                       const void* x, void* y) {
+  if (!hh) return STMG_ERR_ARG;
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (level < 0 || level >= (int)h->levels.size() || !U_state || !x || !y || x == y || U_state == y)
+    return h->fail(STMG_ERR_ARG, "stmg_apply: bad level or pointer");
+  const Level& lv = h->levels[level];
+  cudaError_t e;
+  if (precision == STMG_FP64)
+    e = launch_operator<double>(lv, h->pb, false, 0.0, (const double*)x, (const double*)U_state,
+                                nullptr, (double*)y, h->stream);
+  else if (precision == STMG_FP32)
+    e = launch_operator<float>(lv, h->pb, false, 0.0, (const float*)x, (const float*)U_state,
+                               nullptr, (float*)y, h->stream);
+  else
+    return h->fail(STMG_ERR_ARG, "stmg_apply: bad precision");
+  if (e != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string("stmg_apply: ") + cudaGetErrorString(e));
+  return STMG_OK;
+}
+
+stmg_status stmg_residual(stmg_handle* hh, double t_start, const double* U, const double* V_prev,
+                          double* R) {
+  if (!hh) return STMG_ERR_ARG;
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!U || !V_prev || !R || R == U) return h->fail(STMG_ERR_ARG, "stmg_residual: bad pointer");
+  cudaError_t e = launch_operator<double>(h->levels[0], h->pb, true, t_start, U, nullptr, V_prev, R, h->stream);
+  if (e != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string("stmg_residual: ") + cudaGetErrorString(e));
+  return STMG_OK;
+}
+
+stmg_status stmg_initial_condition(stmg_handle* hh, double* V0) {
+  if (!hh) return STMG_ERR_ARG;
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!V0) return h->fail(STMG_ERR_ARG, "stmg_initial_condition: null pointer");
+  cudaError_t e = launch_initial_condition(h->levels[0], h->pb, V0, h->stream);
+  if (e != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string("stmg_initial_condition: ") + cudaGetErrorString(e));
+  return STMG_OK;
+}
+
+}  // extern "C"

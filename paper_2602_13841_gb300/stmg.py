@@ -1,0 +1,160 @@
+"""ctypes binding of libstmg.so (include/stmg.h).  Argument marshalling only: every step of
+the computation runs in the library's CUDA kernels.  Vectors are torch CUDA tensors passed by
+data_ptr(); the handle's stream defaults to torch's current stream at creation."""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "libstmg.so")
+_lib = None
+
+STMG_FP64, STMG_FP32 = 0, 1
+PROBLEMS = {"TG2D": 0, "MMS2D": 1, "TG3D": 2, "MMS3D": 3}
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NOT_CONVERGED",
+          5: "ERR_NUMERIC", 6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
+
+
+class StmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("n_cells_1d", ctypes.c_int), ("r", ctypes.c_int), ("k", ctypes.c_int),
+        ("nu", ctypes.c_double), ("tau", ctypes.c_double), ("gamma1", ctypes.c_double),
+        ("gamma2", ctypes.c_double), ("problem", ctypes.c_int), ("bconv", ctypes.c_int),
+        ("n_levels_h", ctypes.c_int), ("precond_precision", ctypes.c_int),
+        ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
+        ("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
+        ("ew_eta0", ctypes.c_double), ("ew_c", ctypes.c_double), ("ew_theta", ctypes.c_double),
+        ("ew_min", ctypes.c_double), ("ew_max", ctypes.c_double),
+        ("ls_lambda0", ctypes.c_double), ("ls_c", ctypes.c_double), ("ls_tau", ctypes.c_double),
+        ("ls_alpha_min", ctypes.c_double), ("ls_maxbt", ctypes.c_int), ("ls_window", ctypes.c_int),
+        ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
+        ("rebuild_thetaN", ctypes.c_double), ("rebuild_thetaL", ctypes.c_double),
+        ("rebuild_kappa_abs", ctypes.c_int),
+        ("stag_s", ctypes.c_int), ("stag_theta", ctypes.c_double),
+    ]
+
+
+def load():
+    """Load libstmg.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIBPATH):
+        raise RuntimeError("libstmg.so is missing; run paper_2602_13841_gb300.build.build()")
+    lib = ctypes.CDLL(LIBPATH)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    I64p = ctypes.POINTER(ctypes.c_int64)
+    Ip = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "stmg_params_default": (None, [ctypes.POINTER(Params)]),
+        "stmg_create": (I, [ctypes.POINTER(Params), P, P, ctypes.POINTER(P)]),
+        "stmg_destroy": (None, [P]),
+        "stmg_last_error": (ctypes.c_char_p, [P]),
+        "stmg_num_levels": (I, [P, Ip]),
+        "stmg_level_info": (I, [P, I, Ip, Ip, Ip, I64p, I64p, I64p]),
+        "stmg_apply": (I, [P, I, I, V, V, V]),
+        "stmg_residual": (I, [P, D, V, V, V]),
+        "stmg_initial_condition": (I, [P, V]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_params(**kw):
+    lib = load()
+    p = Params()
+    lib.stmg_params_default(ctypes.byref(p))
+    for key, val in kw.items():
+        if key == "problem" and isinstance(val, str):
+            val = PROBLEMS[val]
+        setattr(p, key, val)
+    return p
+
+
+def _ptr(t, dtype, numel, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError("%s: expected contiguous %s of %d elements, got %s %s" %
+                         (name, dtype, numel, t.dtype, tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One handle: mesh hierarchy and reference tables for one (d, n, r, k) configuration."""
+
+    def __init__(self, params, vertices=None, stream=None):
+        import torch
+        self.lib = load()
+        self.params = params
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        vp = None
+        if vertices is not None:
+            self._verts = np.ascontiguousarray(vertices, dtype=np.float64)
+            vp = self._verts.ctypes.data_as(ctypes.c_void_p)
+        h = ctypes.c_void_p()
+        st = self.lib.stmg_create(ctypes.byref(params), vp, ctypes.c_void_p(stream), ctypes.byref(h))
+        if st != 0:
+            raise StmgError(st, "stmg_create failed")
+        self.h = h
+        nl = ctypes.c_int()
+        self.lib.stmg_num_levels(self.h, ctypes.byref(nl))
+        self.levels = [self.level_info(l) for l in range(nl.value)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.stmg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != 0:
+            raise StmgError(st, "%s: %s" % (what, self.lib.stmg_last_error(self.h).decode()))
+
+    def level_info(self, level):
+        n, r, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        nv, np_, nst = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.stmg_level_info(self.h, level, ctypes.byref(n), ctypes.byref(r), ctypes.byref(k),
+                                             ctypes.byref(nv), ctypes.byref(np_), ctypes.byref(nst)), "level_info")
+        return dict(n=n.value, r=r.value, k=k.value, Nv=nv.value, Np=np_.value, Nst=nst.value)
+
+    def _dtype(self, precision):
+        import torch
+        return torch.float64 if precision == STMG_FP64 else torch.float32
+
+    def apply(self, U, x, y, level=0, precision=STMG_FP64):
+        n = self.levels[level]["Nst"]
+        dt = self._dtype(precision)
+        self._check(self.lib.stmg_apply(self.h, level, precision, _ptr(U, dt, n, "U"), _ptr(x, dt, n, "x"),
+                                        _ptr(y, dt, n, "y")), "apply")
+
+    def residual(self, t_start, U, Vprev, R):
+        import torch
+        L = self.levels[0]
+        self._check(self.lib.stmg_residual(self.h, float(t_start), _ptr(U, torch.float64, L["Nst"], "U"),
+                                           _ptr(Vprev, torch.float64, L["Nv"], "Vprev"),
+                                           _ptr(R, torch.float64, L["Nst"], "R")), "residual")
+
+    def initial_condition(self, V0):
+        import torch
+        self._check(self.lib.stmg_initial_condition(self.h, _ptr(V0, torch.float64, self.levels[0]["Nv"], "V0")),
+                    "initial_condition")
