@@ -112,6 +112,63 @@ stmg_status stmg_residual(stmg_handle* h, double t_start, const double* U, const
  * level): V0 receives n_v doubles (device). */
 stmg_status stmg_initial_condition(stmg_handle* h, double* V0);
 
+/* Newton initial guess: U (n_st doubles, device) gets V_prev (n_v doubles, device) at every
+ * time node and zero pressure. */
+stmg_status stmg_initial_guess(stmg_handle* h, const double* V_prev, double* U);
+
+/* y = diag(M^tau (x) M_h, M^tau (x) M_h^p) x on the finest level, FP64: the matrix of the
+ * mass-weighted norm of Sec. 4.1.  x, y: n_st doubles (device), y may not alias x. */
+stmg_status stmg_mass(stmg_handle* h, const double* x, double* y);
+
+/* Build the hp-STMG preconditioner at the Newton state U (n_st doubles, device, finest level):
+ * level states by interpolation, the inexact Vanka patch inverses of every smoothed level
+ * (midpoint surrogate, Eq. DefTildeHn / DefVnAst, patches = all DoFs of a cell at all time
+ * nodes, Eq. LVS) and the coarsest-level factorisation.  Work space is allocated on the first
+ * call and kept by the handle.  STMG_ERR_UNSUPPORTED if a patch does not fit on-chip memory
+ * for this (d, r, k); STMG_ERR_NUMERIC on a singular patch. */
+stmg_status stmg_smoother_build(stmg_handle* h, const double* U);
+
+/* nsweeps additive Vanka sweeps on a level (Eq. vanka0): d <- d + omega sum_K R_K^T S~_K^{-1}
+ * R_K (rhs - J d), with J the level Jacobian at the level state.  rhs, d: that level's n_st
+ * entries in the preconditioner precision (float for STMG_FP32, double for STMG_FP64);
+ * zero_start = 1 sets d = 0 first.  The level must have a smoother (not the coarsest). */
+stmg_status stmg_smoother_sweep(stmg_handle* h, int level, const void* rhs, void* d, int nsweeps,
+                                int zero_start);
+
+/* One V-cycle of the preconditioner on the finest level: z = B^{-1} r (Sec. 4.2; p-coarsening
+ * first, then h; nu1 / nu2 sweeps; restriction = transpose of prolongation; direct coarse
+ * solve).  r, z: n_st doubles (device); cast to the preconditioner precision internally. */
+stmg_status stmg_vcycle(stmg_handle* h, const double* r, double* z);
+
+/* Grid transfer between `level` and `level + 1`, preconditioner precision:
+ *   op 0: out(level) = P in(level+1)          (prolongation, Sec. 4.2 canonical embedding)
+ *   op 1: out(level+1) = P^T in(level)        (restriction)
+ *   op 2: out(level+1) = I in(level)          (velocity state: fine field at coarse nodes and
+ *                                              Radau points; only the velocity part is written) */
+stmg_status stmg_transfer(stmg_handle* h, int level, int op, const void* in, void* out);
+
+/* Copy the level state of the last smoother build (n_st entries of that level, preconditioner
+ * precision) into out. */
+stmg_status stmg_level_state(stmg_handle* h, int level, void* out);
+
+typedef struct {
+  int newton_its, gmres_its_total, rebuilds, armijo_backtracks;
+  double res0, res_final;                       /* ||R||_M at the start and the end */
+  double t_rebuild, t_vanka, t_mg_other, t_other; /* seconds; filled when timing is on */
+} stmg_stats;
+
+/* Record device time of the four phases of the paper's breakdown (rebuild Vanka, apply Vanka,
+ * rest of multigrid, other) during stmg_slab_solve (adds a few event records per phase). */
+stmg_status stmg_set_timing(stmg_handle* h, int on);
+
+/* Newton-FGMRES solve of one slab (Alg. 1-2): U (n_st doubles, device) is the initial guess on
+ * entry and the solution on return; V_prev (n_v doubles, device) is the velocity at t_start.
+ * Stops at ||R||_M <= max(newton_atol, newton_rtol ||R_0||_M).  STMG_ERR_NOT_CONVERGED when
+ * newton_maxit is reached (U holds the last iterate), STMG_ERR_NUMERIC on NaN / Inf.  stats
+ * may be NULL. */
+stmg_status stmg_slab_solve(stmg_handle* h, double t_start, const double* V_prev, double* U,
+                            stmg_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

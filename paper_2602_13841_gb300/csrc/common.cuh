@@ -57,7 +57,11 @@ struct LevelArgs {
   const T* verts;      // (n+1)^d * d vertex coordinates, vertex-major
   int n, N1;
   int64_t nnodes, Nv, Np;
-  T nu, gamma1, gamma2, hfac;   // hfac = p (p+1), p = r+1 (degree scaling of h_{Gamma_D})
+  T nu, gamma1, gamma2;
+  // h_{Gamma_D} = |K| / |F| * hscale.  Finest level: hscale = 1 / (p (p+1)), p = r+1 (degree-scaled
+  // interior-penalty length).  Coarser levels keep the finest level's penalty: hscale =
+  // (n_level / n_finest) / (p0 (p0+1)), so the penalty term is the Galerkin product of the fine one.
+  T hscale;
   int bconv, problem;
   T t0, tau;
 };

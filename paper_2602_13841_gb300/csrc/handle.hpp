@@ -1,14 +1,31 @@
-// The opaque handle behind stmg_handle: parameters, stream, levels and device allocations.
+// The opaque handle behind stmg_handle: parameters, stream, levels, multigrid, Krylov and
+// Newton work space, phase timers.
 #pragma once
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
 #include "../../include/stmg.h"
 #include "level.hpp"
+#include "mg.hpp"
 
 namespace stmg {
+
+// Accumulates device time of one phase from CUDA event pairs recorded on the handle's stream.
+struct PhaseTimer {
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans;
+  size_t used = 0;
+  double ms = 0.0;
+  cudaEvent_t get();
+  void begin(cudaStream_t s);
+  void end(cudaStream_t s);
+  void collect();            // after a stream synchronisation: add the spans to ms
+  ~PhaseTimer();
+  cudaEvent_t open_ = nullptr;
+};
 
 struct Handle {
   stmg_params prm{};
@@ -17,9 +34,22 @@ struct Handle {
   std::vector<Level> levels;
   std::vector<void*> allocs;
   std::string err;
+  // preconditioner (one of the two, by prm.precond_precision)
+  std::unique_ptr<MG<float>> mg32;
+  std::unique_ptr<MG<double>> mg64;
+  // outer FP64 work space (level 0)
+  double *Vb = nullptr, *Zb = nullptr, *w = nullptr, *R = nullptr, *dX = nullptr, *Xt = nullptr;
+  double *Mv = nullptr, *Jv = nullptr, *pw = nullptr, *scratch = nullptr, *hdev = nullptr;
+  int* flag = nullptr;
+  bool solver_ready = false;
+  bool timing = false;
+  PhaseTimer t_rebuild, t_vanka, t_mg, t_outer;
   ~Handle();
   void* dalloc(size_t bytes);          // cudaMalloc tracked for release; throws std::bad_alloc
   stmg_status fail(stmg_status s, const std::string& msg);
+  cudaError_t ensure_mg();
+  cudaError_t ensure_solver();
+  bool precond_fp32() const { return prm.precond_precision == STMG_FP32; }
 };
 
 }  // namespace stmg

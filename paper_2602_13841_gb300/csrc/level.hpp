@@ -21,6 +21,7 @@ struct Level {
   int* bcells[8]{};                   // device lists of boundary cells per colour
   int nbcells[8]{};
   int ncolors = 0;
+  double hscale = 0;                  // Nitsche length factor (see LevelArgs)
 };
 
 struct Problem {
@@ -31,11 +32,15 @@ struct Problem {
 template <typename T>
 LevelArgs<T> level_args(const Level& lv, const Problem& pb, double t0);
 
-// y (+)= operator(x): J(state) x when res == false, R(x; vprev) when res == true.  y is zeroed
-// first.  Enqueued on `stream`; returns the first CUDA error.
+enum OpMode { OP_JAC = 0, OP_RES = 1, OP_MASS = 2 };
+
+// y = operator(x): J(state) x (OP_JAC), R(x; vprev) (OP_RES, FP64 only) or the slab mass
+// diag(w_a M_h, w_a M_p) x (OP_MASS).  With batch > 1, column b reads x + b*xs and writes
+// y + b*ys (the state is shared).  y is zeroed first.  Enqueued on `stream`.
 template <typename T>
-cudaError_t launch_operator(const Level& lv, const Problem& pb, bool res, double t0, const T* x,
-                            const T* state, const T* vprev, T* y, cudaStream_t stream);
+cudaError_t launch_operator(const Level& lv, const Problem& pb, int mode, double t0, const T* x,
+                            const T* state, const T* vprev, T* y, cudaStream_t stream,
+                            int batch = 1, int64_t xs = 0, int64_t ys = 0);
 
 cudaError_t launch_initial_condition(const Level& lv, const Problem& pb, double* V0, cudaStream_t s);
 

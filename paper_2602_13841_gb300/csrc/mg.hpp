@@ -1,0 +1,64 @@
+// hp space-time multigrid preconditioner (Sec. 4.2-4.3) on the device, element type T of the
+// preconditioner (float: mixed precision; double: plain FP64).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "level.hpp"
+#include "transfer.hpp"
+
+namespace stmg {
+
+struct Handle;
+
+template <typename T>
+struct MG {
+  Handle* h = nullptr;
+  int nl = 0;
+  std::vector<T*> U, r, z, t, q;     // per level: state, rhs, correction, temporaries
+  std::vector<T*> inv;               // per smoothed level: patch inverses
+  std::vector<Transfer> tr;
+  T *EA = nullptr, *EB = nullptr, *EM = nullptr, *vstar = nullptr;
+  int* status = nullptr;             // device flag: zero pivot in a patch
+  // coarsest level: bordered Jacobian (FP64), its FP32 inverse, FP64 refinement buffers
+  int Nc = 0, Nb = 0;
+  double *A64 = nullptr, *Ucs = nullptr, *cb = nullptr, *cx = nullptr, *cr = nullptr, *cw = nullptr;
+  double* ident = nullptr;
+  float* Ainv = nullptr;
+  float* gj_col = nullptr;
+  int* gj_piv = nullptr;
+  bool built = false;
+
+  cudaError_t allocate(Handle* h);
+  // Level states from the fine FP64 slab state, patch inverses on every smoothed level,
+  // coarse factorisation.  Returns cudaErrorUnknown if a patch has a zero pivot.
+  cudaError_t setup(const double* U64);
+  // z = B^{-1} rhs on level 0 (rhs, z: level-0 vectors of type T).
+  cudaError_t vcycle(const T* rhs, T* z);
+  cudaError_t vcycle_level(int l, const T* rhs, T* d);
+  // nsweeps Vanka sweeps on level l: d <- d + omega sum_K ... (rhs - J d); `zero_start`: d = 0 on entry.
+  cudaError_t sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start);
+  cudaError_t coarse_solve(const T* rhs, T* d);
+};
+
+// Launch helpers implemented in vanka.cu (templated on T).
+template <typename T>
+cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar, T* EA, T* EB, T* EM,
+                        T* inv, int* status, cudaStream_t s);
+template <typename T>
+cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const T* res, T* d, double omega,
+                        int color, cudaStream_t s);
+size_t vanka_patch_size(const Level& lv);            // m_st
+size_t vanka_elem_size(const Level& lv, int which);  // entries per cell of EA (0), EB (1), EM (2)
+bool vanka_supported(const Level& lv, size_t esize);
+
+// Coarse solver helpers (coarse.cu)
+cudaError_t coarse_border(const Level& lv, const Problem& pb, const double* J, double* A, int N, int Nb,
+                          cudaStream_t s);
+cudaError_t coarse_invert(const double* A, float* Ainv, float* col, int* piv, int Nb, int* status,
+                          cudaStream_t s);
+cudaError_t gemv_cm(const double* A, int n, const double* x, double* y, cudaStream_t s);
+cudaError_t gemv_cm(const float* A, int n, const double* x, double* y, cudaStream_t s);
+
+}  // namespace stmg

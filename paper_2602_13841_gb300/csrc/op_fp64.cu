@@ -6,11 +6,12 @@
 namespace stmg {
 
 template <>
-cudaError_t launch_operator<double>(const Level& lv, const Problem& pb, bool res, double t0,
+cudaError_t launch_operator<double>(const Level& lv, const Problem& pb, int mode, double t0,
                                     const double* x, const double* state, const double* vprev,
-                                    double* y, cudaStream_t s) {
-  if (res) return launch_any<double, true>(lv, pb, t0, x, state, vprev, y, s);
-  return launch_any<double, false>(lv, pb, t0, x, state, vprev, y, s);
+                                    double* y, cudaStream_t s, int batch, int64_t xs, int64_t ys) {
+  if (mode == OP_RES) return launch_any<double, MR>(lv, pb, t0, x, state, vprev, y, s, batch, xs, ys);
+  if (mode == OP_MASS) return launch_any<double, MM>(lv, pb, t0, x, state, vprev, y, s, batch, xs, ys);
+  return launch_any<double, MJ>(lv, pb, t0, x, state, vprev, y, s, batch, xs, ys);
 }
 
 // v_{0,h}: v0 evaluated at the mapped Gauss-Lobatto nodes (one thread per global node).

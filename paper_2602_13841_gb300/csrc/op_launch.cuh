@@ -12,17 +12,16 @@ LevelArgs<T> level_args(const Level& lv, const Problem& pb, double t0) {
   a.n = lv.n; a.N1 = lv.N1;
   a.nnodes = lv.nnodes; a.Nv = lv.Nv; a.Np = lv.Np;
   a.nu = (T)pb.nu; a.gamma1 = (T)pb.gamma1; a.gamma2 = (T)pb.gamma2;
-  const int p = lv.r + 1;
-  a.hfac = (T)(p * (p + 1));
+  a.hscale = (T)lv.hscale;
   a.bconv = pb.bconv; a.problem = pb.problem;
   a.t0 = (T)t0; a.tau = (T)pb.tau;
   return a;
 }
 
-template <typename T, int D, int N, bool RES>
+template <typename T, int D, int N, int MODE>
 static int vol_smem_per_cell(int kp1) {
   constexpr int Q = Shape<D, N>::Q;
-  return ((RES ? 2 : 3) * kp1 * D * Q + D * D * Q + 2 * D * Q + Q + kp1 * MAXNP + 8 * 3) * (int)sizeof(T);
+  return ((MODE == MJ ? 3 : 2) * kp1 * D * Q + D * D * Q + 2 * D * Q + Q + kp1 * MAXNP + 8 * 3) * (int)sizeof(T);
 }
 
 template <typename T, int D, int N>
@@ -32,52 +31,60 @@ static int face_smem_per_cell(int kp1) {
   return (2 * kp1 * D * Q + kp1 * MAXNP + D * NF + D * D * NF + NF + Q + 4 + 8 * 3) * (int)sizeof(T);
 }
 
-template <typename T, int D, int N, bool RES>
+template <typename T, int D, int N, int MODE>
 static cudaError_t launch_dn(const Level& lv, const Problem& pb, double t0, const T* x,
-                             const T* state, const T* vprev, T* y, cudaStream_t stream) {
+                             const T* state, const T* vprev, T* y, cudaStream_t stream,
+                             int batch, int64_t xs, int64_t ys) {
   constexpr int Q = Shape<D, N>::Q;
   const int kp1 = lv.k + 1;
   Tab<T> tb = make_tab<T>(lv.tabs, pb.tau);
-  OpArgs<T> A{level_args<T>(lv, pb, t0), x, state, vprev, y};
+  OpArgs<T> A{level_args<T>(lv, pb, t0), x, state, vprev, y, xs, ys};
   int cpb = 256 / Q; if (cpb < 1) cpb = 1;
-  int smem = cpb * vol_smem_per_cell<T, D, N, RES>(kp1);
-  while (smem > 160 * 1024 && cpb > 1) { --cpb; smem = cpb * vol_smem_per_cell<T, D, N, RES>(kp1); }
-  cudaError_t e = cudaFuncSetAttribute(k_volume<T, D, N, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int smem = cpb * vol_smem_per_cell<T, D, N, MODE>(kp1);
+  while (smem > 160 * 1024 && cpb > 1) { --cpb; smem = cpb * vol_smem_per_cell<T, D, N, MODE>(kp1); }
+  cudaError_t e = cudaFuncSetAttribute(k_volume<T, D, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int fcpb = 256 / Q; if (fcpb < 1) fcpb = 1;
   int fsmem = fcpb * face_smem_per_cell<T, D, N>(kp1);
   while (fsmem > 160 * 1024 && fcpb > 1) { --fcpb; fsmem = fcpb * face_smem_per_cell<T, D, N>(kp1); }
-  e = cudaFuncSetAttribute(k_faces<T, D, N, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(y, 0, sizeof(T) * lv.Nst, stream);
-  if (e != cudaSuccess) return e;
+  if (MODE != MM) {
+    e = cudaFuncSetAttribute(k_faces<T, D, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem);
+    if (e != cudaSuccess) return e;
+  }
+  for (int b = 0; b < batch; ++b) {
+    e = cudaMemsetAsync(y + b * ys, 0, sizeof(T) * lv.Nst, stream);
+    if (e != cudaSuccess) return e;
+  }
   for (int c = 0; c < lv.ncolors; ++c) {
     const ColorInfo& ci = lv.colors[c];
     if (ci.count > 0) {
-      int blocks = (ci.count + cpb - 1) / cpb;
-      k_volume<T, D, N, RES><<<blocks, cpb * Q, smem, stream>>>(A, tb, ci, cpb);
+      dim3 grid((ci.count + cpb - 1) / cpb, batch);
+      k_volume<T, D, N, MODE><<<grid, cpb * Q, smem, stream>>>(A, tb, ci, cpb);
     }
-    if (lv.nbcells[c] > 0) {
-      int blocks = (lv.nbcells[c] + fcpb - 1) / fcpb;
-      k_faces<T, D, N, RES><<<blocks, fcpb * Q, fsmem, stream>>>(A, tb, lv.bcells[c], lv.nbcells[c], fcpb);
+    if (MODE != MM && lv.nbcells[c] > 0) {
+      dim3 grid((lv.nbcells[c] + fcpb - 1) / fcpb, batch);
+      k_faces<T, D, N, MODE><<<grid, fcpb * Q, fsmem, stream>>>(A, tb, lv.bcells[c], lv.nbcells[c], fcpb);
     }
   }
   return cudaGetLastError();
 }
 
-template <typename T, bool RES>
+template <typename T, int MODE>
 static cudaError_t launch_any(const Level& lv, const Problem& pb, double t0, const T* x,
-                              const T* state, const T* vprev, T* y, cudaStream_t s) {
+                              const T* state, const T* vprev, T* y, cudaStream_t s,
+                              int batch, int64_t xs, int64_t ys) {
   const int N = lv.r + 2;
+#define STMG_LAUNCH(DD, NN) return launch_dn<T, DD, NN, MODE>(lv, pb, t0, x, state, vprev, y, s, batch, xs, ys)
   if (lv.d == 2) {
-    if (N == 3) return launch_dn<T, 2, 3, RES>(lv, pb, t0, x, state, vprev, y, s);
-    if (N == 4) return launch_dn<T, 2, 4, RES>(lv, pb, t0, x, state, vprev, y, s);
-    if (N == 5) return launch_dn<T, 2, 5, RES>(lv, pb, t0, x, state, vprev, y, s);
+    if (N == 3) STMG_LAUNCH(2, 3);
+    if (N == 4) STMG_LAUNCH(2, 4);
+    if (N == 5) STMG_LAUNCH(2, 5);
   } else {
-    if (N == 3) return launch_dn<T, 3, 3, RES>(lv, pb, t0, x, state, vprev, y, s);
-    if (N == 4) return launch_dn<T, 3, 4, RES>(lv, pb, t0, x, state, vprev, y, s);
-    if (N == 5) return launch_dn<T, 3, 5, RES>(lv, pb, t0, x, state, vprev, y, s);
+    if (N == 3) STMG_LAUNCH(3, 3);
+    if (N == 4) STMG_LAUNCH(3, 4);
+    if (N == 5) STMG_LAUNCH(3, 5);
   }
+#undef STMG_LAUNCH
   return cudaErrorInvalidValue;
 }
 

@@ -68,6 +68,7 @@ struct OpArgs {
   const T* state;    // J: the Newton state U (velocity part read); R: unused
   const T* vprev;    // R: V_{n-1}
   T* y;              // output (accumulated)
+  int64_t xs, ys;    // batch strides (blockIdx.y selects the column of a batched apply)
 };
 
 template <int D>
@@ -92,18 +93,22 @@ __device__ inline void load_corners(const LevelArgs<T>& L, const int* cc, T (*co
 }
 
 // ---------------------------------------------------------------------------- volume kernel
-template <typename T, int D, int N, bool RES>
+enum { MJ = 0, MR = 1, MM = 2 };   // Jacobian apply, residual, mass (w_a M_h, w_a M_p)
+
+template <typename T, int D, int N, int MODE>
 __global__ void k_volume(OpArgs<T> A, Tab<T> tb, ColorInfo ci, int cpb) {
+  constexpr bool RES = (MODE == MR);
+  constexpr bool MASS = (MODE == MM);
   constexpr int Q = Shape<D, N>::Q;
   const int kp1 = tb.k + 1, npc = tb.npc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int g = threadIdx.x / Q, t = threadIdx.x % Q;
-  const int per = (RES ? 2 : 3) * kp1 * D * Q + D * D * Q + 2 * D * Q + Q + kp1 * MAXNP + 8 * 3;
+  const int per = (MODE == MJ ? 3 : 2) * kp1 * D * Q + D * D * Q + 2 * D * Q + Q + kp1 * MAXNP + 8 * 3;
   T* s_val = sm + g * per;                        // [kp1][D][Q] increment values at qp
   T* s_tmp = s_val + kp1 * D * Q;                 // [kp1][D][Q]
   T* s_st = s_tmp + kp1 * D * Q;                  // [kp1][D][Q] state values (J only)
-  T* s_F = s_st + (RES ? 0 : kp1 * D * Q);        // [D][D][Q] reference fluxes
+  T* s_F = s_st + (MODE == MJ ? kp1 * D * Q : 0);  // [D][D][Q] reference fluxes
   T* s_z = s_F + D * D * Q;                       // [D][Q] value integrand
   T* s_z2 = s_z + D * Q;                          // [D][Q] temp for the integration passes
   T* s_sp = s_z2 + D * Q;                         // [Q] pressure integrand
@@ -112,6 +117,8 @@ __global__ void k_volume(OpArgs<T> A, Tab<T> tb, ColorInfo ci, int cpb) {
 
   const int cidx = blockIdx.x * cpb + g;
   const bool on = (g < cpb) && (cidx < ci.count);
+  A.x += blockIdx.y * A.xs;
+  A.y += blockIdx.y * A.ys;
   int cc[3] = {0, 0, 0};
   if (on) decode_color_cell<D>(ci, cidx, cc);
   const LevelArgs<T>& L = A.L;
@@ -127,14 +134,14 @@ __global__ void k_volume(OpArgs<T> A, Tab<T> tb, ColorInfo ci, int cpb) {
       for (int c = 0; c < D; ++c) {
         int64_t gi = (int64_t)b * L.Nv + c * L.nnodes + gnode;
         s_val[(b * D + c) * Q + t] = A.x[gi];
-        if (!RES) s_st[(b * D + c) * Q + t] = A.state[gi];
+        if (MODE == MJ) s_st[(b * D + c) * Q + t] = A.state[gi];
       }
     if (t < npc)
       for (int b = 0; b < kp1; ++b) s_pm[b * MAXNP + t] = A.x[poff + (int64_t)b * L.Np + cell * npc + t];
   }
   __syncthreads();
   tensor_pass<T, D, N, false>(s_val, s_tmp, tb.B, t, kp1 * D, on);
-  if (!RES) tensor_pass<T, D, N, false>(s_st, s_tmp, tb.B, t, kp1 * D, on);
+  if (MODE == MJ) tensor_pass<T, D, N, false>(s_st, s_tmp, tb.B, t, kp1 * D, on);
 
   // geometry at quadrature point t
   int tq[3];
@@ -189,14 +196,14 @@ __global__ void k_volume(OpArgs<T> A, Tab<T> tb, ColorInfo ci, int cpb) {
       T dv[3], v[3];
       for (int c = 0; c < D; ++c) {
         dv[c] = va[c * Q + t];
-        v[c] = RES ? dv[c] : s_st[(a * D + c) * Q + t];
+        v[c] = (MODE == MJ) ? s_st[(a * D + c) * Q + t] : dv[c];
       }
       const T wa = tb.w[a];
       T F[3][3];
       for (int c = 0; c < D; ++c)
         for (int l = 0; l < D; ++l) {
           T conv = RES ? v[c] * v[l] : dv[c] * v[l] + v[c] * dv[l];
-          F[c][l] = L.nu * gp[c][l] - conv - ((c == l) ? pq : (T)0);
+          F[c][l] = MASS ? (T)0 : L.nu * gp[c][l] - conv - ((c == l) ? pq : (T)0);
         }
       for (int c = 0; c < D; ++c)
         for (int m = 0; m < D; ++m) {
@@ -214,13 +221,17 @@ __global__ void k_volume(OpArgs<T> A, Tab<T> tb, ColorInfo ci, int cpb) {
       }
       for (int c = 0; c < D; ++c) {
         T acc = 0;
-        for (int b = 0; b < kp1; ++b) acc += tb.K[a][b] * s_val[(b * D + c) * Q + t];
+        if (MASS) {
+          acc = wa * dv[c];
+        } else {
+          for (int b = 0; b < kp1; ++b) acc += tb.K[a][b] * s_val[(b * D + c) * Q + t];
+        }
         if (RES) acc -= tb.C[a] * vprev_q[c] + wa * fq[c];
         s_z[c * Q + t] = JxW * acc;
       }
       T div = 0;
       for (int c = 0; c < D; ++c) div += gp[c][c];
-      s_sp[t] = -wa * JxW * div;
+      s_sp[t] = MASS ? wa * JxW * pq : -wa * JxW * div;
     }
     __syncthreads();
     // z_c += sum_m Dc_m^T F_cm (gradient test functions at the Gauss points)
@@ -264,7 +275,7 @@ __global__ void k_volume(OpArgs<T> A, Tab<T> tb, ColorInfo ci, int cpb) {
 //               + (y+ - 2y-) dv_c + (3 - sgn y)/2 (dv.n) v_c],  b_c = -w_a nu dv_c,  s = w_a dv.n
 //   R: a_c = w_a[-nu d_n v_c + nu g1/h e_c + g2/h (e.n) n_c + p n_c + (y+ - 2y-) v_c + (g.n)- g_c],
 //      b_c = -w_a nu e_c,  s = w_a e.n,  e = v - g
-// with y = v.n, tested as  a_c z_c + b_c d_n z_c  and  s q.  h = |K| / |F| / (p(p+1)).
+// with y = v.n, tested as  a_c z_c + b_c d_n z_c  and  s q.  h = |K| / |F| * hscale (hscale = 1/(p(p+1)) on the finest level, see LevelArgs).
 template <typename T, int D, int N>
 __device__ inline void face_weights(const Tab<T>& tb, int axis, int side, const int* pq, int j,
                                     T& val, T* grad) {
@@ -294,7 +305,7 @@ __device__ inline T face_psi(const Tab<T>& tb, int axis, int side, const int* pq
   return psi;
 }
 
-template <typename T, int D, int N, bool RES>
+template <typename T, int D, int N, int MODE>
 __global__ void k_faces(OpArgs<T> A, Tab<T> tb, const int* __restrict__ bcells, int nb, int cpb) {
   constexpr int Q = Shape<D, N>::Q;
   constexpr int NF = Shape<D, N>::NF;
@@ -313,9 +324,12 @@ __global__ void k_faces(OpArgs<T> A, Tab<T> tb, const int* __restrict__ bcells, 
   T* s_sc = s_red + Q;                   // [4]: volume, area
   T(*corner)[3] = reinterpret_cast<T(*)[3]>(s_sc + 4);
 
+  constexpr bool RES = (MODE == MR);
   const int bi = blockIdx.x * cpb + g;
   const bool on = (g < cpb) && (bi < nb);
   const LevelArgs<T>& L = A.L;
+  A.x += blockIdx.y * A.xs;
+  A.y += blockIdx.y * A.ys;
   int cc[3] = {0, 0, 0};
   int64_t cell = 0;
   if (on) {
@@ -376,7 +390,7 @@ __global__ void k_faces(OpArgs<T> A, Tab<T> tb, const int* __restrict__ bcells, 
       __syncthreads();
       if (has && t == 0) { T v = 0; for (int p = 0; p < NF; ++p) v += s_red[p]; s_sc[1] = v; }
       __syncthreads();
-      const T h = has ? s_sc[0] / s_sc[1] / L.hfac : (T)1;
+      const T h = has ? s_sc[0] / s_sc[1] * L.hscale : (T)1;
       for (int a = 0; a < kp1; ++a) {
         if (has && t < NF) {
           T dv[3] = {0, 0, 0}, v[3] = {0, 0, 0}, gref[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};

@@ -109,7 +109,7 @@ void stmg_params_default(stmg_params* p) {
   p->nu = 1e-2; p->tau = 0.1; p->gamma1 = 10.0; p->gamma2 = 10.0;
   p->problem = STMG_TG2D; p->bconv = 1; p->n_levels_h = -1;
   p->precond_precision = STMG_FP32;
-  p->nu1 = 1; p->nu2 = 1; p->omega = 0.7;
+  p->nu1 = 1; p->nu2 = 1; p->omega = 0.3;
   p->newton_rtol = 1e-8; p->newton_atol = 1e-12; p->newton_maxit = 20;
   p->ew_eta0 = 0.4; p->ew_c = 0.5; p->ew_theta = 1.5; p->ew_min = 1e-3; p->ew_max = 0.8;
   p->ls_lambda0 = 1.0; p->ls_c = 1e-4; p->ls_tau = 0.5; p->ls_alpha_min = 1e-3;
@@ -155,8 +155,10 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
       else { r /= 2; k /= 2; }
       pk.push_back({r, k});
     }
+    const double p0 = p->r + 1;
     for (auto& rk : pk) {
       Level lv; lv.d = d; lv.n = n; lv.r = rk.first; lv.k = rk.second;
+      lv.hscale = 1.0 / (p0 * (p0 + 1.0));
       build_level(h.get(), lv, verts);
       h->levels.push_back(lv);
     }
@@ -166,6 +168,7 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
       cv = coarsen_vertices(cv, d, nn);
       nn /= 2; ++hl;
       Level lv; lv.d = d; lv.n = nn; lv.r = r; lv.k = k;
+      lv.hscale = ((double)nn / n) / (p0 * (p0 + 1.0));
       build_level(h.get(), lv, cv);
       h->levels.push_back(lv);
     }
@@ -218,10 +221,10 @@ stmg_status stmg_apply(stmg_handle* hh, int level, int precision, const void* U_
   const Level& lv = h->levels[level];
   cudaError_t e;
   if (precision == STMG_FP64)
-    e = launch_operator<double>(lv, h->pb, false, 0.0, (const double*)x, (const double*)U_state,
+    e = launch_operator<double>(lv, h->pb, OP_JAC, 0.0, (const double*)x, (const double*)U_state,
                                 nullptr, (double*)y, h->stream);
   else if (precision == STMG_FP32)
-    e = launch_operator<float>(lv, h->pb, false, 0.0, (const float*)x, (const float*)U_state,
+    e = launch_operator<float>(lv, h->pb, OP_JAC, 0.0, (const float*)x, (const float*)U_state,
                                nullptr, (float*)y, h->stream);
   else
     return h->fail(STMG_ERR_ARG, "stmg_apply: bad precision");
@@ -234,7 +237,7 @@ stmg_status stmg_residual(stmg_handle* hh, double t_start, const double* U, cons
   if (!hh) return STMG_ERR_ARG;
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!U || !V_prev || !R || R == U) return h->fail(STMG_ERR_ARG, "stmg_residual: bad pointer");
-  cudaError_t e = launch_operator<double>(h->levels[0], h->pb, true, t_start, U, nullptr, V_prev, R, h->stream);
+  cudaError_t e = launch_operator<double>(h->levels[0], h->pb, OP_RES, t_start, U, nullptr, V_prev, R, h->stream);
   if (e != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string("stmg_residual: ") + cudaGetErrorString(e));
   return STMG_OK;
 }

@@ -41,6 +41,16 @@ class Params(ctypes.Structure):
     ]
 
 
+class Stats(ctypes.Structure):
+    _fields_ = [("newton_its", ctypes.c_int), ("gmres_its_total", ctypes.c_int), ("rebuilds", ctypes.c_int),
+                ("armijo_backtracks", ctypes.c_int), ("res0", ctypes.c_double), ("res_final", ctypes.c_double),
+                ("t_rebuild", ctypes.c_double), ("t_vanka", ctypes.c_double), ("t_mg_other", ctypes.c_double),
+                ("t_other", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 def load():
     """Load libstmg.so; raises if it has not been built (no fallback path exists)."""
     global _lib
@@ -62,6 +72,15 @@ def load():
         "stmg_apply": (I, [P, I, I, V, V, V]),
         "stmg_residual": (I, [P, D, V, V, V]),
         "stmg_initial_condition": (I, [P, V]),
+        "stmg_initial_guess": (I, [P, V, V]),
+        "stmg_mass": (I, [P, V, V]),
+        "stmg_smoother_build": (I, [P, V]),
+        "stmg_smoother_sweep": (I, [P, I, V, V, I, I]),
+        "stmg_vcycle": (I, [P, V, V]),
+        "stmg_transfer": (I, [P, I, I, V, V]),
+        "stmg_level_state": (I, [P, I, V]),
+        "stmg_set_timing": (I, [P, I]),
+        "stmg_slab_solve": (I, [P, D, V, V, ctypes.POINTER(Stats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -158,3 +177,63 @@ class Solver:
         import torch
         self._check(self.lib.stmg_initial_condition(self.h, _ptr(V0, torch.float64, self.levels[0]["Nv"], "V0")),
                     "initial_condition")
+
+    # -------------------------------------------------------------- solver
+    @property
+    def pdtype(self):
+        import torch
+        return torch.float32 if self.params.precond_precision == STMG_FP32 else torch.float64
+
+    def initial_guess(self, Vprev, U):
+        import torch
+        L = self.levels[0]
+        self._check(self.lib.stmg_initial_guess(self.h, _ptr(Vprev, torch.float64, L["Nv"], "Vprev"),
+                                                _ptr(U, torch.float64, L["Nst"], "U")), "initial_guess")
+
+    def mass(self, x, y):
+        import torch
+        n = self.levels[0]["Nst"]
+        self._check(self.lib.stmg_mass(self.h, _ptr(x, torch.float64, n, "x"), _ptr(y, torch.float64, n, "y")), "mass")
+
+    def smoother_build(self, U):
+        import torch
+        self._check(self.lib.stmg_smoother_build(self.h, _ptr(U, torch.float64, self.levels[0]["Nst"], "U")),
+                    "smoother_build")
+
+    def smoother_sweep(self, level, rhs, d, nsweeps=1, zero_start=False):
+        n = self.levels[level]["Nst"]
+        self._check(self.lib.stmg_smoother_sweep(self.h, level, _ptr(rhs, self.pdtype, n, "rhs"),
+                                                 _ptr(d, self.pdtype, n, "d"), nsweeps, int(zero_start)),
+                    "smoother_sweep")
+
+    def vcycle(self, r, z):
+        import torch
+        n = self.levels[0]["Nst"]
+        self._check(self.lib.stmg_vcycle(self.h, _ptr(r, torch.float64, n, "r"), _ptr(z, torch.float64, n, "z")),
+                    "vcycle")
+
+    def transfer(self, level, op, x, y):
+        """op 0: prolongation (level+1 -> level); 1: restriction; 2: state interpolation."""
+        nf, nc = self.levels[level]["Nst"], self.levels[level + 1]["Nst"]
+        nin, nout = (nc, nf) if op == 0 else (nf, nc)
+        self._check(self.lib.stmg_transfer(self.h, level, op, _ptr(x, self.pdtype, nin, "in"),
+                                           _ptr(y, self.pdtype, nout, "out")), "transfer")
+
+    def level_state(self, level, out):
+        self._check(self.lib.stmg_level_state(self.h, level, _ptr(out, self.pdtype, self.levels[level]["Nst"], "out")),
+                    "level_state")
+
+    def set_timing(self, on=True):
+        self._check(self.lib.stmg_set_timing(self.h, int(on)), "set_timing")
+
+    def slab_solve(self, t_start, Vprev, U, check=True):
+        """Newton-FGMRES solve of one slab; U is the initial guess and receives the solution.
+        Returns (status, stats dict); raises on failure when check is true."""
+        import torch
+        L = self.levels[0]
+        st = Stats()
+        rc = self.lib.stmg_slab_solve(self.h, float(t_start), _ptr(Vprev, torch.float64, L["Nv"], "Vprev"),
+                                      _ptr(U, torch.float64, L["Nst"], "U"), ctypes.byref(st))
+        if check:
+            self._check(rc, "slab_solve")
+        return rc, st.as_dict()

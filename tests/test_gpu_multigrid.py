@@ -1,0 +1,136 @@
+"""GPU parity of the hp-STMG preconditioner and the Newton-FGMRES slab solve (through the C ABI).
+
+Against the oracle (same seeded inputs, FP64 preconditioner on the GPU unless stated):
+* prolongation, restriction and state interpolation of every level pair: 1e-13 relative;
+* the level states of a smoother build: 1e-13 relative;
+* Vanka sweeps (from zero and from a nonzero iterate) on every smoothed level: 1e-9 relative
+  (the patch inverses are Gauss-Jordan on the GPU, LU on the oracle; patches are ill-conditioned);
+* one V-cycle: 1e-8 relative (coarse solve: FP32 inverse plus FP64 iterative refinement);
+* slab solves reach the Newton tolerance, and the GPU solution (FP64 or FP32 preconditioner)
+  equals the exact discrete solution (oracle Newton with sparse direct solves) to 1e-7 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import forms, marching, multigrid, problems
+from oracle.reference import TimeData
+from paper_2602_13841_gb300 import inputs
+from tests.helpers import build_and_load, have_gpu
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not have_gpu(), reason="needs a CUDA GPU")]
+
+
+def _t(a, dtype=None):
+    import torch
+    return torch.tensor(np.asarray(a), dtype=dtype or torch.float64, device="cuda")
+
+
+def _np(t):
+    return t.double().cpu().numpy()
+
+
+def _setup(d, n, r, k, amp, precision="fp64", omega=0.3, nu=0.01, tau=0.05, problem="TG2D", seed=5, **kw):
+    from paper_2602_13841_gb300 import stmg
+    build_and_load()
+    verts = inputs.vertices(d, n, amp, seed)
+    prec = stmg.STMG_FP64 if precision == "fp64" else stmg.STMG_FP32
+    p = stmg.default_params(dim=d, n_cells_1d=n, r=r, k=k, nu=nu, tau=tau, problem=problem,
+                            omega=omega, precond_precision=prec, **kw)
+    S = stmg.Solver(p, verts)
+    mg = multigrid.Multigrid(d, n, r, k, verts, tau, nu, omega=omega)
+    return S, mg, verts
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("d,n,r,k,amp,prec", [(2, 8, 2, 2, 0.15, "fp64"), (2, 6, 3, 1, 0.0, "fp64"),
+                                              (3, 4, 1, 1, 0.1, "fp32"), (3, 4, 2, 1, 0.1, "fp32")])
+def test_transfers_match_oracle(d, n, r, k, amp, prec):
+    import torch
+    S, mg, _ = _setup(d, n, r, k, amp, precision=prec)
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    dt = S.pdtype
+    assert [(L["n"], L["r"], L["k"]) for L in S.levels] == [(L.n, L.r, L.k) for L in mg.levels]
+    for l in range(len(mg.levels) - 1):
+        f, c = mg.levels[l], mg.levels[l + 1]
+        xc = inputs.uniform(c.Nst, 100 + l)
+        xf = inputs.uniform(f.Nst, 200 + l)
+        out = torch.empty(f.Nst, dtype=dt, device="cuda")
+        S.transfer(l, 0, _t(xc, dt), out)
+        assert _rel(_np(out), mg.P[l] @ xc) < tol
+        outc = torch.empty(c.Nst, dtype=dt, device="cuda")
+        S.transfer(l, 1, _t(xf, dt), outc)
+        assert _rel(_np(outc), mg.P[l].T @ xf) < tol
+        outc.zero_()
+        S.transfer(l, 2, _t(xf, dt), outc)
+        nvc = (c.k + 1) * c.lay.Nv
+        assert _rel(_np(outc)[:nvc], mg.I[l] @ xf[:(f.k + 1) * f.lay.Nv]) < tol
+
+
+@pytest.mark.parametrize("d,n,r,k,amp,prec", [(2, 8, 2, 2, 0.15, "fp64"), (2, 8, 1, 1, 0.0, "fp64"),
+                                              (2, 6, 1, 0, 0.1, "fp64"), (2, 8, 2, 2, 0.15, "fp32"),
+                                              (3, 4, 1, 1, 0.1, "fp32")])
+def test_smoother_and_vcycle_match_oracle(d, n, r, k, amp, prec):
+    """FP64: tight tolerances.  FP32 (the mixed-precision preconditioner): the error of each
+    result against the FP64 oracle is bounded by 2e-3 relative (ill-conditioned patches)."""
+    import torch
+    S, mg, _ = _setup(d, n, r, k, amp, precision=prec)
+    dt = S.pdtype
+    tol_s, tol_v, tol_x = (1e-9, 1e-8, 1e-13) if prec == "fp64" else (2e-3, 2e-3, 2e-6)
+    L0 = mg.levels[0]
+    U = inputs.uniform(L0.Nst, 7)
+    mg.setup(U)
+    S.smoother_build(_t(U))
+    for l, L in enumerate(mg.levels):
+        st = torch.empty(L.Nst, dtype=dt, device="cuda")
+        S.level_state(l, st)
+        nv = (L.k + 1) * L.lay.Nv
+        assert _rel(_np(st)[:nv], mg.states[l][:nv]) < tol_x
+    for l in range(len(mg.levels) - 1):
+        L = mg.levels[l]
+        rhs = inputs.uniform(L.Nst, 30 + l)
+        d0 = inputs.uniform(L.Nst, 40 + l)
+        want = mg.smoothers[l].sweep(mg.J[l], rhs, np.zeros(L.Nst))
+        got = torch.empty(L.Nst, dtype=dt, device="cuda")
+        S.smoother_sweep(l, _t(rhs, dt), got, 1, zero_start=True)
+        assert _rel(_np(got), want) < tol_s, l
+        want = mg.smoothers[l].sweep(mg.J[l], rhs, d0)
+        got = _t(d0, dt)
+        S.smoother_sweep(l, _t(rhs, dt), got, 1, zero_start=False)
+        assert _rel(_np(got), want) < tol_s, l
+    r0 = inputs.uniform(L0.Nst, 77)
+    z = torch.empty(L0.Nst, dtype=torch.float64, device="cuda")
+    S.vcycle(_t(r0), z)
+    assert _rel(_np(z), mg.vcycle(r0)) < tol_v
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("d,n,r,k,amp,nu,tau,pname", [
+    (2, 8, 1, 1, 0.0, 1e-2, 0.1, "TG2D"),       # 2D 8x8, Q2/P1, DG(1), dt = 0.1, Re = 100
+    (2, 8, 2, 2, 0.1, 1e-3, 0.05, "TG2D"),      # small case of the Q3/P2/DG(2) mapped workload
+    (2, 8, 1, 2, 0.1, 1e-2, 0.1, "MMS2D"),
+])
+def test_slab_solve_reaches_tolerance_and_matches_exact_solution(precision, d, n, r, k, amp, nu, tau, pname):
+    import torch
+    S, mg, verts = _setup(d, n, r, k, amp, precision=precision, nu=nu, tau=tau, problem=pname,
+                          newton_rtol=1e-10)
+    L0 = mg.levels[0]
+    prob = problems.make(pname, nu)
+    V0 = torch.empty(L0.lay.Nv, dtype=torch.float64, device="cuda")
+    S.initial_condition(V0)
+    U = torch.empty(L0.Nst, dtype=torch.float64, device="cuda")
+    S.initial_guess(V0, U)
+    t0 = 0.2
+    rc, st = S.slab_solve(t0, V0, U)
+    assert rc == 0 and st["res_final"] <= 1e-10 * st["res0"]
+    assert 1 <= st["newton_its"] <= 12 and st["rebuilds"] >= 1
+    Vp = _np(V0)
+    U0 = np.concatenate([np.tile(Vp, k + 1), np.zeros((k + 1) * L0.lay.Np)])
+    Ud, _ = marching.newton_direct(L0.space, L0.td, U0, Vp, prob, t0, tol=1e-13)
+    nv = (k + 1) * L0.lay.Nv
+    got = _np(U)
+    assert _rel(got[:nv], Ud[:nv]) < 1e-7
+    # pressure: same up to the mean, which both remove
+    assert np.abs(got[nv:] - Ud[nv:]).max() < 1e-6 * max(np.abs(Ud[nv:]).max(), 1.0)
