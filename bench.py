@@ -1,0 +1,293 @@
+"""Benchmark: Newton-GMRES slab solves with the hp-STMG preconditioner on one GB300.
+
+Workload (the configuration the metric is quoted on): 2D unit square, 256 x 256 cells on a
+mapped mesh (smooth seeded sinusoidal vertex perturbation, amplitude 0.1 h, seed 1234),
+Q3/P2^disc (r = 2), DG(2), slabs of dt = 0.05, Re = 1000 Taylor-Green vortex, FP32 hp-STMG
+preconditioner inside FP64 Newton-FGMRES, Newton tolerance 1e-10 relative.
+
+One step = one slab solve (residual, Jacobian applies, smoother rebuilds, V-cycles, FGMRES,
+Newton with Armijo): the whole hot path.  K steps march K consecutive slabs from t = 0
+(K = 4 is the full 4-slab configuration).  value = space-time DoFs solved per second
+(sum of N_st over the K slabs / device time).  Inputs are resident in HBM when the timed
+region starts; the working set (Vanka patch inverses, 3.4 GB) exceeds the L2 cache.
+e2e: the same solves through the C ABI with the step's input (V_prev) copied from pinned host
+memory and the result (U) copied back inside the timed region.
+
+`--impl reference` times the FP64 CPU oracle (test infrastructure, plain numpy) on a bounded
+sample of the same workload on the host cores.  With torchrun, every rank runs an independent
+replica (the slab solve does not shard); rank 0 prints the JSON line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ST operator apply GDoF/s; Newton-GMRES slab-solve time; serving p50/p99 latency"
+WORKLOAD = dict(d=2, n=256, r=2, k=2, amp=0.1, seed=1234, nu=1e-3, tau=0.05, problem="TG2D")
+WORKLOAD_NAME = ("2D unit square 256x256 mapped (amp 0.1h, seed 1234), Q3/P2disc (r=2), DG(2), "
+                 "dt=0.05, Re=1000 Taylor-Green; FP32 hp-STMG in FP64 Newton-FGMRES, rtol 1e-10")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.stop = threading.Event()
+        self.t = None
+
+    def _run(self):
+        while not self.stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self.stop.wait(0.2)
+
+    def __enter__(self):
+        self.t = threading.Thread(target=self._run, daemon=True)
+        self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop.set()
+        self.t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(n=16, slabs=1):
+    """FP64 CPU oracle slab solves on a bounded sample: the workload's (d, r, k, dt, Re, mesh
+    recipe) on an n x n mesh.  Returns (DoF/s, seconds, N_st, description)."""
+    from oracle import forms, krylov, problems
+    from paper_2602_13841_gb300 import inputs
+    w = WORKLOAD
+    prob = problems.make(w["problem"], w["nu"])
+    verts = inputs.vertices(w["d"], n, w["amp"], w["seed"])
+    S = krylov.SlabSolver(w["d"], n, w["r"], w["k"], verts, w["tau"], prob, omega=0.3, rtol=1e-10)
+    L = S.L
+    Vprev = forms.interpolate_velocity(L.space, prob.v0)
+    t = time.perf_counter()
+    for sl in range(slabs):
+        U0 = np.concatenate([np.tile(Vprev, w["k"] + 1), np.zeros((w["k"] + 1) * L.lay.Np)])
+        X, st = S.solve(U0, Vprev, sl * w["tau"])
+        Vprev = L.lay.v(X, w["k"]).copy()
+    dt = time.perf_counter() - t
+    desc = ("oracle Newton-FGMRES-hpSTMG slab solve, %dx%d mesh of the same recipe, r=%d, k=%d, %d slab(s), "
+            "N_st=%d" % (n, n, w["r"], w["k"], slabs, L.Nst))
+    return L.Nst * slabs / dt, dt, L.Nst, desc
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(n=8)
+    vals = []
+    t_tot = 0.0
+    for _ in range(args.steps):
+        v, dt, nst, desc = oracle_sample(n=args.ref_n)
+        vals.append(v)
+        t_tot += dt
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": _cpu_cores(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-n", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_2602_13841_gb300 import build, inputs, stmg
+    build.build()
+    w = WORKLOAD
+    p = stmg.default_params(dim=w["d"], n_cells_1d=w["n"], r=w["r"], k=w["k"], nu=w["nu"], tau=w["tau"],
+                            problem=w["problem"], precond_precision=stmg.STMG_FP32, newton_rtol=1e-10,
+                            omega=0.3)
+    stream = torch.cuda.Stream(device=dev)
+    S = stmg.Solver(p, inputs.vertices(w["d"], w["n"], w["amp"], w["seed"]), stream=stream.cuda_stream)
+    L = S.levels[0]
+    Nst, Nv, k = L["Nst"], L["Nv"], w["k"]
+    with torch.cuda.stream(stream):
+        V0 = torch.empty(Nv, dtype=torch.float64, device=dev)
+        S.initial_condition(V0)
+        Vp = torch.empty_like(V0)
+        U = torch.empty(Nst, dtype=torch.float64, device=dev)
+
+    def march(nslabs, timed_events=None, stats=None):
+        Vp.copy_(V0)
+        for sl in range(nslabs):
+            if timed_events is not None:
+                timed_events[sl][0].record(stream)
+            S.initial_guess(Vp, U)
+            rc, st = S.slab_solve(sl * w["tau"], Vp, U)
+            Vp.copy_(U[k * Nv:(k + 1) * Nv])
+            if timed_events is not None:
+                timed_events[sl][1].record(stream)
+            if stats is not None:
+                stats.append(st)
+
+    with torch.cuda.stream(stream):
+        march(args.warmup)
+    torch.cuda.synchronize(dev)
+    lib = stmg.load()
+    launches0 = lib.stmg_launch_count()
+    S.set_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk, torch.cuda.stream(stream):
+        march(args.steps, ev, stats)
+        torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    launches = lib.stmg_launch_count() - launches0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * Nst * args.steps / (ms * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    S.set_timing(False)
+    hV = torch.empty(Nv, dtype=torch.float64).pin_memory()
+    hU = torch.empty(Nst, dtype=torch.float64).pin_memory()
+    hV.copy_(V0.cpu())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for sl in range(args.steps):
+            Vp.copy_(hV, non_blocking=True)
+            S.initial_guess(Vp, U)
+            S.slab_solve(sl * w["tau"], Vp, U)
+            hU.copy_(U, non_blocking=True)
+            stream.synchronize()
+            hV.copy_(hU[k * Nv:(k + 1) * Nv])
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_e2e = e0.elapsed_time(e1)
+    e2e = {"value": ws * Nst * args.steps / (ms_e2e * 1e-3), "unit": "DoF/s",
+           "h2d_bytes_per_step": Nv * 8, "d2h_bytes_per_step": Nst * 8}
+
+    # ---- roofline of the dominant kernel (Vanka patch apply, HBM-bound) from the live timers
+    prof = S.kernel_profile()
+    roof = roofline(S, prof)
+    buckets = {key: float(np.sum([st[key] for st in stats])) for key in ("t_rebuild", "t_vanka", "t_mg_other", "t_other")}
+    peaks = _peaks()
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            v, dt, nst, desc = oracle_sample(n=16)
+            cpu = {"value": v, "unit": "DoF/s", "cores": _cpu_cores(), "kind": "oracle", "sample": desc}
+        line = {
+            "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "N_st": Nst, "slabs_per_step": 1,
+                       "l2": "working set larger than L2 (Vanka patch inverses 3.4 GB)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "solver": {"newton_its": [st["newton_its"] for st in stats],
+                       "gmres_its": [st["gmres_its_total"] for st in stats],
+                       "rebuilds": [st["rebuilds"] for st in stats],
+                       "res_ratio": [st["res_final"] / st["res0"] for st in stats]},
+            "phase_seconds": buckets, "kernels": prof, "peaks": peaks,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def roofline(S, prof):
+    """Vanka patch apply: per colour launch it reads the patch inverses of its cells (m_st^2
+    values), the residual and the correction on the patch DoFs, and writes the correction."""
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    k = prof.get("vanka_apply")
+    if not k or not k["count"]:
+        return None
+    return {"bound": "hbm", "kernel": "k_vanka_apply", "achieved": k["bytes"] / (k["ms"] * 1e-3) / 1e9,
+            "peak": hbm, "unit": "GB/s", "frac": k["bytes"] / (k["ms"] * 1e-3) / 1e9 / hbm,
+            "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+            "launches": k["count"], "avg_us": 1e3 * k["ms"] / k["count"]}
+
+
+if __name__ == "__main__":
+    main()

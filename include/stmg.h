@@ -161,6 +161,18 @@ typedef struct {
  * rest of multigrid, other) during stmg_slab_solve (adds a few event records per phase). */
 stmg_status stmg_set_timing(stmg_handle* h, int on);
 
+/* Device time (ms), launches and algorithmic bytes accumulated per kernel class while timing is
+ * on (collected at the end of each stmg_slab_solve).  Classes: 0 FP64 Jacobian apply (outer
+ * FGMRES), 1 preconditioner-precision Jacobian apply (level residuals), 2 residual, 3 Vanka
+ * patch apply (one launch per colour; bytes = patch inverses + patch vectors), 4 Vanka build
+ * (element matrices, patch assembly and inversion), 5 mass apply. */
+stmg_status stmg_kernel_profile(const stmg_handle* h, int cls, double* ms, long long* launches,
+                                double* bytes);
+stmg_status stmg_kernel_profile_reset(stmg_handle* h);
+
+/* Number of kernels this library has launched in this process (all handles). */
+long long stmg_launch_count(void);
+
 /* Newton-FGMRES solve of one slab (Alg. 1-2): U (n_st doubles, device) is the initial guess on
  * entry and the solution on return; V_prev (n_v doubles, device) is the velocity at t_start.
  * Stops at ||R||_M <= max(newton_atol, newton_rtol ||R_0||_M).  STMG_ERR_NOT_CONVERGED when

@@ -76,7 +76,7 @@ def pressure_at(space, P, psi):
 
 
 # ----------------------------------------------------------------------------- residual
-def residual(space, td, U, Vprev, prob, t0, gamma1=10.0, gamma2=10.0, bconv=True):
+def residual(space, td, U, Vprev, prob, t0, gamma1=10.0, gamma2=10.0, bconv=True, hscale=None):
     """R_n(U; V_{n-1}) of Eq. InAlgNS (LHS minus RHS), FP64."""
     lay = SlabLayout(space, td.k)
     d, nu = space.d, prob.nu
@@ -109,7 +109,7 @@ def residual(space, td, U, Vprev, prob, t0, gamma1=10.0, gamma2=10.0, bconv=True
                 g = prob.g(fd["x"], ti)
                 nrm = fd["normal"]
                 JxWf = fd["JxW"]
-                h = nitsche_length(space, JxWf)
+                h = nitsche_length(space, JxWf, hscale)
                 dnv = np.einsum("kpcl,kpl->kpc", gvf, nrm)
                 e = vf - g
                 en = np.einsum("kpc,kpc->kp", e, nrm)
@@ -141,8 +141,11 @@ def residual(space, td, U, Vprev, prob, t0, gamma1=10.0, gamma2=10.0, bconv=True
     return R
 
 
-def nitsche_length(space, face_JxW):
+def nitsche_length(space, face_JxW, hscale=None):
     """h_{Gamma_D} of Eq. def-b-gam-3 per cell for one face: h_F / (p (p+1)), p = r+1.
+
+    `hscale` replaces the factor 1 / (p (p+1)); the multigrid levels pass the finest level's
+    value times n_level / n_finest, so that every level keeps the finest level's penalty.
 
     h_F = |K| / |F| (cell volume over the area of this face).  The paper does not define
     h_{Gamma_D}.  With the plain h_F and gamma_1 = gamma_2 = 10 the discrete problem is not
@@ -151,7 +154,9 @@ def nitsche_length(space, face_JxW):
     reproduces the errors printed in Table conv-ns.
     """
     p = space.r + 1
-    return space.cell_volume / face_JxW.sum(axis=1) / (p * (p + 1))
+    if hscale is None:
+        hscale = 1.0 / (p * (p + 1))
+    return space.cell_volume / face_JxW.sum(axis=1) * hscale
 
 
 def _boundary_cells(space, axis, side):
@@ -160,7 +165,7 @@ def _boundary_cells(space, axis, side):
 
 
 # ----------------------------------------------------------------------------- element matrices
-def element_matrices(space, V, nu, gamma1=10.0, gamma2=10.0, bconv=True):
+def element_matrices(space, V, nu, gamma1=10.0, gamma2=10.0, bconv=True, hscale=None):
     """Per-cell spatial matrices of one time node at velocity state V.
 
     Returns A [cells, d*nloc, d*nloc] = nu A_h + N^{b,r}(gamma) + H'(V) + N^c'(V) (velocity block,
@@ -186,7 +191,7 @@ def element_matrices(space, V, nu, gamma1=10.0, gamma2=10.0, bconv=True):
             cells = _boundary_cells(space, axis, side)
             fd = space.face_data[(axis, side)]
             JxWf, nrm, fphi, fgphi = fd["JxW"], fd["normal"], fd["phi"], fd["gphi"]
-            h = nitsche_length(space, JxWf)
+            h = nitsche_length(space, JxWf, hscale)
             vf, _ = velocity_at_face(space, V, axis, side)
             y = np.einsum("kpc,kpc->kp", vf, nrm)
             dn = np.einsum("kpjl,kpl->kpj", fgphi, nrm)
@@ -245,7 +250,7 @@ def _scatter_block(rows_idx, cols_idx, blocks):
     return r, c, blocks.ravel()
 
 
-def jacobian(space, td, U, nu, gamma1=10.0, gamma2=10.0, bconv=True, vstar=None):
+def jacobian(space, td, U, nu, gamma1=10.0, gamma2=10.0, bconv=True, vstar=None, hscale=None):
     """Assembled slab Jacobian J_n(U) (Eq. JacobianLocal0-1) as a CSR matrix.
 
     With `vstar` given, every time node's convection Jacobian is evaluated at the single
@@ -261,7 +266,7 @@ def jacobian(space, td, U, nu, gamma1=10.0, gamma2=10.0, bconv=True, vstar=None)
                 cols.append(Mv.col + lay.voff(a))
                 vals.append(td.K[i, a] * Mv.data)
         Vs = lay.v(U, i) if vstar is None else vstar
-        A, B = element_matrices(space, Vs, nu, gamma1, gamma2, bconv)
+        A, B = element_matrices(space, Vs, nu, gamma1, gamma2, bconv, hscale)
         wi = td.w[i]
         vd = space.cell_vdofs
         pd = space.cell_pdofs

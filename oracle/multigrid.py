@@ -12,7 +12,11 @@ space-time Vanka smoother), restated as plain assembled linear algebra:
   fine Legendre modes; time: coarse Lagrange polynomial at the fine Radau points);
 * restriction R = P^T;
 * level state: the fine velocity evaluated at the coarse nodes and Radau points;
-* level operator: the Jacobian rediscretised at the level state;
+* level operator: the Jacobian rediscretised at the level state, with the finest level's
+  Nitsche penalty length on every level (h_{Gamma_D} scaled by n_level / n_finest and the
+  finest degree factor), which makes the penalty term of the level operator equal to its
+  Galerkin product P^T A P on nested meshes; with the level's own h and degree the coarse
+  penalty is too weak and the V-cycle diverges;
 * Vanka (Eq. LVS, vanka0): additive over cells, patch = all velocity and pressure DoFs of the
   cell at all time nodes, patch matrix = the global submatrix R_K J~ R_K^T of the midpoint
   surrogate J~ (Eq. DefTildeHn, DefVnAst), inverted by dense LU with partial pivoting;
@@ -144,8 +148,9 @@ def time_prolongation(kf, kc):
 
 
 class Level:
-    def __init__(self, d, n, r, k, vertices, tau, nu, gamma=(10.0, 10.0), bconv=True):
+    def __init__(self, d, n, r, k, vertices, tau, nu, gamma=(10.0, 10.0), bconv=True, hscale=None):
         self.d, self.n, self.r, self.k = d, n, r, k
+        self.hscale = hscale
         self.space = Space(Mesh(d, n, vertices), r)
         self.td = TimeData(k, tau)
         self.lay = forms.SlabLayout(self.space, k)
@@ -188,7 +193,8 @@ class Vanka:
     def __init__(self, level, U, omega):
         self.level, self.omega = level, omega
         vstar = midpoint_velocity(level, U)
-        Jt = forms.jacobian(level.space, level.td, U, level.nu, *level.gamma, level.bconv, vstar=vstar)
+        Jt = forms.jacobian(level.space, level.td, U, level.nu, *level.gamma, level.bconv, vstar=vstar,
+                            hscale=level.hscale)
         Jt = Jt.tocsr()
         self.patches = []
         for c in range(level.space.mesh.ncells):
@@ -231,7 +237,8 @@ class Multigrid:
 
     def __init__(self, d, n, r, k, vertices, tau, nu, omega=0.7, nu1=1, nu2=1,
                  gamma=(10.0, 10.0), bconv=True, max_h=-1):
-        self.levels = [Level(d, ln, lr, lk, lv, tau, nu, gamma, bconv)
+        p0 = r + 1
+        self.levels = [Level(d, ln, lr, lk, lv, tau, nu, gamma, bconv, hscale=(ln / n) / (p0 * (p0 + 1)))
                        for ln, lr, lk, lv in hierarchy(d, n, r, k, vertices, max_h)]
         self.P, self.I = [], []
         for f, c in zip(self.levels[:-1], self.levels[1:]):
@@ -253,7 +260,7 @@ class Multigrid:
     def setup(self, U):
         """Level Jacobians, Vanka patches (smoother build) and the coarse factorisation at U."""
         self.states = self.level_states(U)
-        self.J = [forms.jacobian(L.space, L.td, S, L.nu, *L.gamma, L.bconv)
+        self.J = [forms.jacobian(L.space, L.td, S, L.nu, *L.gamma, L.bconv, hscale=L.hscale)
                   for L, S in zip(self.levels, self.states)]
         self.smoothers = [Vanka(L, S, self.omega) for L, S in zip(self.levels[:-1], self.states[:-1])]
         self.coarse = CoarseSolver(self.levels[-1], self.J[-1])

@@ -6,6 +6,7 @@
 #include "mg.hpp"
 #include "op_launch.cuh"
 #include "vanka.cuh"
+#include "counters.hpp"
 
 namespace stmg {
 
@@ -36,14 +37,17 @@ __global__ void k_border_rows(const double* __restrict__ Me, double* __restrict_
 cudaError_t coarse_border(const Level& lv, const Problem& pb, const double* J, double* A, int N, int Nb,
                           cudaStream_t s) {
   k_border_copy<<<152 * 4, 256, 0, s>>>(J, A, N, Nb);
+  note_launch();
   // scratch: the two columns after J (caller allocates Nb*Nb + 2*N for J's buffer)
   double* e = const_cast<double*>(J) + (int64_t)N * N;
   double* Me = e + N;
   for (int a = 0; a <= lv.k; ++a) {
     k_const_pressure<<<64, 256, 0, s>>>(e, (int64_t)(lv.k + 1) * lv.Nv, lv.Np, lv.npc, a, N);
+  note_launch();
     cudaError_t err = launch_operator<double>(lv, pb, OP_MASS, 0.0, e, nullptr, nullptr, Me, s);
     if (err != cudaSuccess) return err;
     k_border_rows<<<64, 256, 0, s>>>(Me, A, N, Nb, a);
+  note_launch();
   }
   return cudaGetLastError();
 }
@@ -72,6 +76,7 @@ __global__ void k_transpose32(float* S, int n) {
 cudaError_t coarse_invert(const double* A, float* Ainv, float* col, int* piv, int Nb, int* status,
                           cudaStream_t s) {
   k_to_rowmajor32<<<152 * 4, 256, 0, s>>>(A, Ainv, Nb);
+  note_launch();
   k_gj_single<<<1, 1024, 0, s>>>(Ainv, Nb, col, piv, status);
   k_transpose32<<<152 * 4, 256, 0, s>>>(Ainv, Nb);    // row-major inverse -> column-major
   return cudaGetLastError();
@@ -88,11 +93,13 @@ __global__ void k_gemv_cm(const TA* __restrict__ A, int n, const double* __restr
 
 cudaError_t gemv_cm(const double* A, int n, const double* x, double* y, cudaStream_t s) {
   k_gemv_cm<double><<<(n + 127) / 128, 128, 0, s>>>(A, n, x, y);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t gemv_cm(const float* A, int n, const double* x, double* y, cudaStream_t s) {
   k_gemv_cm<float><<<(n + 127) / 128, 128, 0, s>>>(A, n, x, y);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -13,6 +13,11 @@
 
 namespace stmg {
 
+// Kernel classes of the profile: FP64 Jacobian apply, preconditioner-precision Jacobian apply,
+// residual, Vanka patch apply (one launch per colour), Vanka build, mass apply.
+enum KernelClass { KC_APPLY64 = 0, KC_APPLYP = 1, KC_RESIDUAL = 2, KC_VANKA_APPLY = 3, KC_VANKA_BUILD = 4,
+                   KC_MASS = 5, KC_COUNT = 6 };
+
 // Accumulates device time of one phase from CUDA event pairs recorded on the handle's stream.
 struct PhaseTimer {
   std::vector<cudaEvent_t> pool;
@@ -44,6 +49,14 @@ struct Handle {
   bool solver_ready = false;
   bool timing = false;
   PhaseTimer t_rebuild, t_vanka, t_mg, t_outer;
+  // per kernel class (KernelClass) device time, launch count and algorithmic bytes, timing mode
+  PhaseTimer kt[8];
+  long long kcount[8] = {};
+  double kbytes[8] = {};
+  void kbegin(int cls) { if (timing) kt[cls].begin(stream); }
+  void kend(int cls, double bytes = 0.0, int launches = 1) {
+    if (timing) { kt[cls].end(stream); kcount[cls] += launches; kbytes[cls] += bytes; }
+  }
   ~Handle();
   void* dalloc(size_t bytes);          // cudaMalloc tracked for release; throws std::bad_alloc
   stmg_status fail(stmg_status s, const std::string& msg);

@@ -5,6 +5,7 @@
 #include "handle.hpp"
 #include "mg.hpp"
 #include "vec.cuh"
+#include "counters.hpp"
 
 namespace stmg {
 
@@ -25,7 +26,7 @@ cudaError_t MG<T>::allocate(Handle* hh) {
       t[l] = (T*)h->dalloc(lv.Nst * sizeof(T));
       q[l] = (T*)h->dalloc(lv.Nst * sizeof(T));
       if (l < nl - 1) {
-        if (!vanka_supported(lv, sizeof(T))) return cudaErrorNotSupported;
+        if (!vanka_supported(lv, sizeof(T))) { smoothable = false; continue; }
         size_t m = vanka_patch_size(lv);
         inv[l] = (T*)h->dalloc((size_t)(lv.Np / lv.npc) * m * m * sizeof(T));
         size_t nc = lv.Np / lv.npc;
@@ -73,6 +74,7 @@ template <typename T>
 cudaError_t MG<T>::setup(const double* U64) {
   cudaStream_t s = h->stream;
   const Level& f = h->levels[0];
+  if (!smoothable) return cudaErrorNotSupported;
   CKE(cudaMemsetAsync(status, 0, sizeof(int), s));
   CKE((vcopy<double, T>(f.Nst, U64, U[0], s)));
   for (int l = 0; l + 1 < nl; ++l) {
@@ -80,12 +82,16 @@ cudaError_t MG<T>::setup(const double* U64) {
     CKE(cudaMemsetAsync(U[l + 1], 0, c.Nst * sizeof(T), s));
     CKE(tr[l].template interp_state<T>(U[l], U[l + 1], s));
   }
-  for (int l = 0; l + 1 < nl; ++l)
+  for (int l = 0; l + 1 < nl; ++l) {
+    h->kbegin(KC_VANKA_BUILD);
     CKE(vanka_build<T>(h->levels[l], h->pb, U[l], vstar, EA, EB, EM, inv[l], status, s));
+    h->kend(KC_VANKA_BUILD, 0.0, 4);
+  }
   // coarse: assemble J_c at the coarse state by a batched apply to the identity
   const Level& c = h->levels[nl - 1];
   CKE((vcopy<T, double>(c.Nst, U[nl - 1], Ucs, s)));
   k_identity<<<152 * 4, 256, 0, s>>>(ident, Nc);
+  note_launch();
   CKE(launch_operator<double>(c, h->pb, OP_JAC, 0.0, ident, Ucs, nullptr, A64, s, Nc, Nc, Nc));
   // A64 now holds J (N x N, column-major); move into the bordered layout via `ident` as staging
   CKE(cudaMemcpyAsync(ident, A64, (size_t)Nc * Nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -126,12 +132,20 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
       CKE(cudaMemsetAsync(d, 0, lv.Nst * sizeof(T), s));
     } else {
       // q = rhs - J d
+      h->kbegin(KC_APPLYP);
       CKE(launch_operator<T>(lv, h->pb, OP_JAC, 0.0, d, U[l], nullptr, q[l], s));
+      h->kend(KC_APPLYP);
       CKE(vaxpby<T>(lv.Nst, (T)1, rhs, (T)-1, q[l], s));
       res = q[l];
     }
     if (h->timing) h->t_vanka.begin(s);
-    for (int c = 0; c < lv.ncolors; ++c) CKE(vanka_apply<T>(lv, h->pb, inv[l], res, d, omega, c, s));
+    const double m = (double)vanka_patch_size(lv);
+    for (int c = 0; c < lv.ncolors; ++c) {
+      // algorithmic bytes: the patch inverses of the colour's cells, residual gather, d update
+      h->kbegin(KC_VANKA_APPLY);
+      CKE(vanka_apply<T>(lv, h->pb, inv[l], res, d, omega, c, s));
+      h->kend(KC_VANKA_APPLY, (double)lv.colors[c].count * (m * m + 3.0 * m) * sizeof(T));
+    }
     if (h->timing) h->t_vanka.end(s);
   }
   return cudaSuccess;
@@ -146,7 +160,9 @@ cudaError_t MG<T>::vcycle_level(int l, const T* rhs, T* d) {
   if (nu1 > 0) CKE(sweep(l, rhs, d, nu1, true));
   else CKE(cudaMemsetAsync(d, 0, lv.Nst * sizeof(T), s));
   // t = rhs - J d ; r_{l+1} = P^T t
+  h->kbegin(KC_APPLYP);
   CKE(launch_operator<T>(lv, h->pb, OP_JAC, 0.0, d, U[l], nullptr, t[l], s));
+  h->kend(KC_APPLYP);
   CKE(vaxpby<T>(lv.Nst, (T)1, rhs, (T)-1, t[l], s));
   CKE(tr[l].template restrict_<T>(t[l], r[l + 1], s));
   CKE(vcycle_level(l + 1, r[l + 1], z[l + 1]));

@@ -29,6 +29,7 @@ struct MG {
   float* gj_col = nullptr;
   int* gj_piv = nullptr;
   bool built = false;
+  bool smoothable = true;            // every smoothed level's patch fits on-chip memory
 
   cudaError_t allocate(Handle* h);
   // Level states from the fine FP64 slab state, patch inverses on every smoothed level,

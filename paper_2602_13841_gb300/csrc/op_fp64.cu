@@ -46,6 +46,7 @@ cudaError_t launch_initial_condition(const Level& lv, const Problem& pb, double*
   int64_t blocks = (lv.nnodes + 255) / 256;
   if (lv.d == 2) k_initial<2><<<(unsigned)blocks, 256, 0, s>>>(L, tb, lv.r + 1, V0);
   else k_initial<3><<<(unsigned)blocks, 256, 0, s>>>(L, tb, lv.r + 1, V0);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 #include "level.hpp"
 #include "operator.cuh"
+#include "counters.hpp"
 
 namespace stmg {
 
@@ -60,10 +61,12 @@ static cudaError_t launch_dn(const Level& lv, const Problem& pb, double t0, cons
     if (ci.count > 0) {
       dim3 grid((ci.count + cpb - 1) / cpb, batch);
       k_volume<T, D, N, MODE><<<grid, cpb * Q, smem, stream>>>(A, tb, ci, cpb);
+      note_launch();
     }
     if (MODE != MM && lv.nbcells[c] > 0) {
       dim3 grid((lv.nbcells[c] + fcpb - 1) / fcpb, batch);
       k_faces<T, D, N, MODE><<<grid, fcpb * Q, fsmem, stream>>>(A, tb, lv.bcells[c], lv.nbcells[c], fcpb);
+      note_launch();
     }
   }
   return cudaGetLastError();

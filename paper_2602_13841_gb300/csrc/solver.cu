@@ -16,6 +16,7 @@
 
 #include "handle.hpp"
 #include "vec.cuh"
+#include "counters.hpp"
 
 namespace stmg {
 
@@ -76,6 +77,7 @@ cudaError_t Handle::ensure_solver() {
   // time node 0 holds w_0 * int psi_m over each cell)
   CKE(cudaMemsetAsync(Mv, 0, L.Nst * sizeof(double), stream));
   k_const_p0<<<64, 256, 0, stream>>>(Mv, (int64_t)(L.k + 1) * L.Nv, L.Np, L.npc);
+  note_launch();
   CKE(launch_operator<double>(L, pb, OP_MASS, 0.0, Mv, nullptr, nullptr, pw, stream));
   solver_ready = true;
   return cudaSuccess;
@@ -91,7 +93,9 @@ static cudaError_t dot_host(Handle* h, int64_t n, const double* a, const double*
 // ||Z||_M = sqrt(Z^T M Z)
 static cudaError_t mnorm(Handle* h, const double* Z, double* out) {
   const Level& L = h->levels[0];
+  h->kbegin(KC_MASS);
   CKE(launch_operator<double>(L, h->pb, OP_MASS, 0.0, Z, nullptr, nullptr, h->Mv, h->stream));
+  h->kend(KC_MASS, 16.0 * L.Nst);
   double v = 0;
   CKE(dot_host(h, L.Nst, Z, h->Mv, &v));
   *out = std::sqrt(v > 0 ? v : 0.0);
@@ -118,9 +122,11 @@ static cudaError_t project_mean(Handle* h, double* U) {
   {
     CKE(cudaMemsetAsync(h->Mv, 0, L.Np * sizeof(double), h->stream));
     k_const_p0<<<64, 256, 0, h->stream>>>(h->Mv, 0, L.Np, L.npc);
+  note_launch();
     CKE(dot_host(h, L.Np, pwp, h->Mv, &vol));
   }
   k_sub_mean<<<64, 256, 0, h->stream>>>(P, L.Np, L.npc, L.k + 1, h->hdev + 224, 1.0 / vol);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -173,7 +179,10 @@ static cudaError_t fgmres(Handle* h, MG<T>& mg, const double* U, const double* b
       double* vj = h->Vb + (int64_t)j * N;
       double* zj = h->Zb + (int64_t)j * N;
       CKE(precondition<T>(h, mg, vj, zj));
+      // algorithmic bytes of the apply: read x and the state velocity, write y (FP64)
+      h->kbegin(KC_APPLY64);
       CKE(launch_operator<double>(L, h->pb, OP_JAC, 0.0, zj, U, nullptr, h->w, s));
+      h->kend(KC_APPLY64, 8.0 * (L.k + 1) * (3.0 * L.Nv + 2.0 * L.Np));
       // CGS2
       CKE(vdots<double>(N, j + 1, h->Vb, N, h->w, h->hdev, h->scratch, s));
       CKE(vsub_comb<double>(N, j + 1, h->Vb, N, h->hdev, h->w, s));
@@ -254,7 +263,7 @@ static stmg_status newton(Handle* h, MG<T>& mg, double t0, const double* Vprev, 
   cudaStream_t s = h->stream;
   const stmg_params& P = h->prm;
   const double eps = 1e-30;
-#define CKS(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return h->fail(e_ == cudaErrorUnknown ? STMG_ERR_NUMERIC : STMG_ERR_CUDA, std::string("slab_solve: ") + #x + ": " + cudaGetErrorString(e_)); } while (0)
+#define CKS(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return h->fail(e_ == cudaErrorUnknown ? STMG_ERR_NUMERIC : e_ == cudaErrorNotSupported ? STMG_ERR_UNSUPPORTED : STMG_ERR_CUDA, std::string("slab_solve: ") + #x + ": " + cudaGetErrorString(e_)); } while (0)
   CKS(launch_operator<double>(L, h->pb, OP_RES, t0, X, nullptr, Vprev, h->R, s));
   double nr = 0;
   CKS(mnorm(h, h->R, &nr));
@@ -357,6 +366,7 @@ stmg_status stmg_smoother_build(stmg_handle* hh, const double* U) {
   if (e != cudaSuccess) return h->fail(e == cudaErrorMemoryAllocation ? STMG_ERR_OOM : STMG_ERR_CUDA, std::string("smoother_build: ") + cudaGetErrorString(e));
   e = h->precond_fp32() ? h->mg32->setup(U) : h->mg64->setup(U);
   if (e == cudaErrorUnknown) return h->fail(STMG_ERR_NUMERIC, "smoother_build: singular patch or coarse matrix");
+  if (e == cudaErrorNotSupported) return h->fail(STMG_ERR_UNSUPPORTED, "smoother_build: patch too large for this configuration");
   if (e != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string("smoother_build: ") + cudaGetErrorString(e));
   return STMG_OK;
 }
@@ -436,6 +446,7 @@ stmg_status stmg_initial_guess(stmg_handle* hh, const double* V_prev, double* U)
   Handle* h = H(hh);
   const Level& L = h->levels[0];
   k_guess<<<152 * 8, 256, 0, h->stream>>>(V_prev, U, L.Nv, L.k + 1, L.Nst);
+  note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string("initial_guess: ") + cudaGetErrorString(e));
   return STMG_OK;
@@ -470,6 +481,7 @@ stmg_status stmg_slab_solve(stmg_handle* hh, double t_start, const double* V_pre
     float tot = 0;
     cudaEventElapsedTime(&tot, e0, e1);
     h->t_rebuild.collect(); h->t_vanka.collect(); h->t_mg.collect();
+    for (int c = 0; c < KC_COUNT; ++c) h->kt[c].collect();
     S->t_rebuild = h->t_rebuild.ms * 1e-3;
     S->t_vanka = h->t_vanka.ms * 1e-3;
     S->t_mg_other = (h->t_mg.ms - h->t_vanka.ms) * 1e-3;

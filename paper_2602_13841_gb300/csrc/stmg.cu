@@ -8,7 +8,10 @@
 #include <string>
 #include <vector>
 
+#include <atomic>
+
 #include "../../include/stmg.h"
+#include "counters.hpp"
 #include "handle.hpp"
 
 using namespace stmg;
@@ -20,6 +23,10 @@ using namespace stmg;
   } while (0)
 
 namespace stmg {
+
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 int height(int x) { int h = 0; while (x > 1) { x /= 2; ++h; } return h; }
 
@@ -115,7 +122,7 @@ void stmg_params_default(stmg_params* p) {
   p->ls_lambda0 = 1.0; p->ls_c = 1e-4; p->ls_tau = 0.5; p->ls_alpha_min = 1e-3;
   p->ls_maxbt = 5; p->ls_window = 5;
   p->gmres_restart = 30; p->gmres_maxit = 50;
-  p->rebuild_thetaN = 0.5; p->rebuild_thetaL = 2.0; p->rebuild_kappa_abs = 20;
+  p->rebuild_thetaN = 1.0; p->rebuild_thetaL = 2.0; p->rebuild_kappa_abs = 20;
   p->stag_s = 3; p->stag_theta = 0.95;
 }
 
@@ -179,6 +186,24 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
   }
   if (cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); return STMG_ERR_CUDA; }
   *out = reinterpret_cast<stmg_handle*>(h.release());
+  return STMG_OK;
+}
+
+long long stmg_launch_count(void) { return launch_count(); }
+
+stmg_status stmg_kernel_profile(const stmg_handle* hh, int cls, double* ms, long long* launches, double* bytes) {
+  if (!hh || cls < 0 || cls >= KC_COUNT) return STMG_ERR_ARG;
+  const Handle* h = reinterpret_cast<const Handle*>(hh);
+  if (ms) *ms = h->kt[cls].ms;
+  if (launches) *launches = h->kcount[cls];
+  if (bytes) *bytes = h->kbytes[cls];
+  return STMG_OK;
+}
+
+stmg_status stmg_kernel_profile_reset(stmg_handle* hh) {
+  if (!hh) return STMG_ERR_ARG;
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  for (int c = 0; c < KC_COUNT; ++c) { h->kt[c].ms = 0; h->kcount[c] = 0; h->kbytes[c] = 0; }
   return STMG_OK;
 }
 

@@ -4,6 +4,7 @@
 
 #include "handle.hpp"
 #include "transfer.hpp"
+#include "counters.hpp"
 
 namespace stmg {
 
@@ -248,6 +249,7 @@ static cudaError_t tensor_apply(const Csr1D& op, int d, int nin, int nout, int b
     if (ax == d - 1) sdst = sout;
     dim3 grid(grid1(outer * nout * inner), batch);
     k_axis<T><<<grid, 256, 0, s>>>(src, dst, (int)ext[ax], nout, inner, outer, sin, sdst, op.rowptr, op.col, vals<T>(op));
+    note_launch();
     ext[ax] = nout;
     src = dst;
     sin = sdst;
@@ -266,6 +268,7 @@ cudaError_t Transfer::prolong(const T* xc, T* xf, cudaStream_t s) const {
   Mat3 M{};
   for (int a = 0; a <= f.k; ++a) for (int b = 0; b <= c.k; ++b) M.m[a][b] = E[a][b];
   k_timemix<T><<<grid1(f.Nv), 256, 0, s>>>(C, xf, f.Nv, c.k + 1, f.k + 1, f.Nv, f.Nv, M);
+  note_launch();
   // pressure
   const T* pc = xc + (int64_t)(c.k + 1) * c.Nv;
   T* pf = xf + (int64_t)(f.k + 1) * f.Nv;
@@ -273,7 +276,9 @@ cudaError_t Transfer::prolong(const T* xc, T* xf, cudaStream_t s) const {
   dim3 g(grid1(ncf * f.npc), c.k + 1);
   if (d == 2) k_pprolong<T, 2><<<g, 256, 0, s>>>(pc, C, f.n, ratio, f.npc, c.npc, ptab<T>(*this), c.Np, f.Np);
   else k_pprolong<T, 3><<<g, 256, 0, s>>>(pc, C, f.n, ratio, f.npc, c.npc, ptab<T>(*this), c.Np, f.Np);
+  note_launch();
   k_timemix<T><<<grid1(f.Np), 256, 0, s>>>(C, pf, f.Np, c.k + 1, f.k + 1, f.Np, f.Np, M);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -285,15 +290,18 @@ cudaError_t Transfer::restrict_(const T* xf, T* xc, cudaStream_t s) const {
   Mat3 M{};
   for (int a = 0; a <= c.k; ++a) for (int b = 0; b <= f.k; ++b) M.m[a][b] = E[b][a];   // E^T
   k_timemix<T><<<grid1(f.Nv), 256, 0, s>>>(xf, C, f.Nv, f.k + 1, c.k + 1, f.Nv, f.Nv, M);
+  note_launch();
   cudaError_t e = tensor_apply<T>(P1T, d, f.N1, c.N1, (c.k + 1) * d, C, xc, A, B, s);
   if (e != cudaSuccess) return e;
   const T* pf = xf + (int64_t)(f.k + 1) * f.Nv;
   T* pc = xc + (int64_t)(c.k + 1) * c.Nv;
   k_timemix<T><<<grid1(f.Np), 256, 0, s>>>(pf, C, f.Np, f.k + 1, c.k + 1, f.Np, f.Np, M);
+  note_launch();
   int64_t ncc = c.Np / c.npc;
   dim3 g(grid1(ncc * c.npc), c.k + 1);
   if (d == 2) k_prestrict<T, 2><<<g, 256, 0, s>>>(C, pc, f.n, ratio, f.npc, c.npc, ptab<T>(*this), f.Np, c.Np);
   else k_prestrict<T, 3><<<g, 256, 0, s>>>(C, pc, f.n, ratio, f.npc, c.npc, ptab<T>(*this), f.Np, c.Np);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -304,6 +312,7 @@ cudaError_t Transfer::interp_state(const T* Vf, T* Vc, cudaStream_t s) const {
   Mat3 M{};
   for (int a = 0; a <= c.k; ++a) for (int b = 0; b <= f.k; ++b) M.m[a][b] = Et[a][b];
   k_timemix<T><<<grid1(f.Nv), 256, 0, s>>>(Vf, C, f.Nv, f.k + 1, c.k + 1, f.Nv, f.Nv, M);
+  note_launch();
   return tensor_apply<T>(I1, f.d, f.N1, c.N1, (c.k + 1) * f.d, C, Vc, A, B, s);
 }
 

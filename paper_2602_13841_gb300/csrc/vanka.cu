@@ -5,6 +5,7 @@
 #include "op_launch.cuh"
 #include "vanka.cuh"
 #include "vec.cuh"
+#include "counters.hpp"
 
 namespace stmg {
 
@@ -75,6 +76,7 @@ static cudaError_t build_dn(const Level& lv, const Problem& pb, const T* U, T* v
   e = cudaFuncSetAttribute(k_patch<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
   if (e != cudaSuccess) return e;
   k_patch<T, D, N><<<(unsigned)ncells, 256, ps, s>>>(V, tb, ncells);
+  note_launch(3);
   return cudaGetLastError();
 }
 
@@ -101,6 +103,7 @@ static cudaError_t apply_dn(const Level& lv, const Problem& pb, const T* inv, co
   size_t smem = sizeof(T) * (((m + 1) & ~1)) + sizeof(int64_t) * m + 16;
   k_vanka_apply<T, D, N><<<ci.count, threads, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, res, d, (T)omega,
                                                          lv.k + 1, lv.npc, ci);
+  note_launch();
   return cudaGetLastError();
 }
 

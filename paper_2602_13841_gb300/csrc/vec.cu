@@ -1,6 +1,7 @@
 // Vector kernels (see vec.cuh).  Grid-stride loops sized as a multiple of the SM count;
 // reductions in a fixed order (block partial sums, then one block per result).
 #include "vec.cuh"
+#include "counters.hpp"
 
 namespace stmg {
 
@@ -20,6 +21,7 @@ __global__ void k_axpby(int64_t n, T a, const T* __restrict__ x, T b, T* __restr
 template <typename T>
 cudaError_t vaxpby(int64_t n, T a, const T* x, T b, T* y, cudaStream_t s) {
   k_axpby<T><<<grid_for(n), 256, 0, s>>>(n, a, x, b, y);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -32,6 +34,7 @@ __global__ void k_copy(int64_t n, const S* __restrict__ x, T* __restrict__ y) {
 template <typename S, typename T>
 cudaError_t vcopy(int64_t n, const S* x, T* y, cudaStream_t s) {
   k_copy<S, T><<<grid_for(n), 256, 0, s>>>(n, x, y);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -72,6 +75,7 @@ cudaError_t vdots(int64_t n, int m, const T* X, int64_t ldx, const T* w, double*
                   cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   k_dots_partial<T><<<dim3(RED_BLOCKS, m), RED_THREADS, 0, s>>>(n, X, ldx, w, scratch);
+  note_launch();
   k_dots_final<<<m, RED_THREADS, 0, s>>>(scratch, out);
   return cudaGetLastError();
 }
@@ -94,6 +98,7 @@ cudaError_t vsub_comb(int64_t n, int m, const T* X, int64_t ldx, const double* h
   if (m <= 0) return cudaSuccess;
   if (m > 64) return cudaErrorInvalidValue;
   k_sub_comb<T><<<grid_for(n), 256, 0, s>>>(n, m, X, ldx, h, w);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -115,6 +120,7 @@ cudaError_t vadd_comb_host(int64_t n, int m, const double* Z, int64_t ldz, const
   Coef64 c{};
   for (int l = 0; l < m; ++l) c.v[l] = y[l];
   k_add_comb<<<grid_for(n), 256, 0, s>>>(n, m, Z, ldz, c, x);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -128,6 +134,7 @@ __global__ void k_scale_inv_dev(int64_t n, const T* __restrict__ x, const double
 template <typename T>
 cudaError_t vscale_inv_dev(int64_t n, const T* x, const double* nrm, T* y, cudaStream_t s) {
   k_scale_inv_dev<T><<<grid_for(n), 256, 0, s>>>(n, x, nrm, y);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -140,6 +147,7 @@ __global__ void k_scale(int64_t n, T a, const T* __restrict__ x, T* __restrict__
 template <typename T>
 cudaError_t vscale(int64_t n, T a, const T* x, T* y, cudaStream_t s) {
   k_scale<T><<<grid_for(n), 256, 0, s>>>(n, a, x, y);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -151,6 +159,7 @@ __global__ void k_fill(int64_t n, T v, T* __restrict__ x) {
 template <typename T>
 cudaError_t vfill(int64_t n, T v, T* x, cudaStream_t s) {
   k_fill<T><<<grid_for(n), 256, 0, s>>>(n, v, x);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -161,6 +170,7 @@ __global__ void k_finite(int64_t n, const double* __restrict__ x, int* flag) {
 
 cudaError_t vfinite(int64_t n, const double* x, int* flag, cudaStream_t s) {
   k_finite<<<grid_for(n), 256, 0, s>>>(n, x, flag);
+  note_launch();
   return cudaGetLastError();
 }
 

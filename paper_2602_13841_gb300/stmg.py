@@ -81,6 +81,10 @@ def load():
         "stmg_level_state": (I, [P, I, V]),
         "stmg_set_timing": (I, [P, I]),
         "stmg_slab_solve": (I, [P, D, V, V, ctypes.POINTER(Stats)]),
+        "stmg_kernel_profile": (I, [P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(ctypes.c_double)]),
+        "stmg_kernel_profile_reset": (I, [P]),
+        "stmg_launch_count": (ctypes.c_longlong, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -225,6 +229,20 @@ class Solver:
 
     def set_timing(self, on=True):
         self._check(self.lib.stmg_set_timing(self.h, int(on)), "set_timing")
+
+    KERNEL_CLASSES = ("apply_fp64", "apply_precond", "residual", "vanka_apply", "vanka_build", "mass")
+
+    def kernel_profile(self, reset=False):
+        """{class: {ms, count, bytes}} accumulated while timing was on."""
+        out = {}
+        for i, name in enumerate(self.KERNEL_CLASSES):
+            ms, cnt, by = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+            self._check(self.lib.stmg_kernel_profile(self.h, i, ctypes.byref(ms), ctypes.byref(cnt),
+                                                     ctypes.byref(by)), "kernel_profile")
+            out[name] = {"ms": ms.value, "count": cnt.value, "bytes": by.value}
+        if reset:
+            self.lib.stmg_kernel_profile_reset(self.h)
+        return out
 
     def slab_solve(self, t_start, Vprev, U, check=True):
         """Newton-FGMRES solve of one slab; U is the initial guess and receives the solution.
