@@ -123,7 +123,7 @@ def run_reference(args):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(n=8)
+        oracle_sample(n=4)
     vals = []
     t_tot = 0.0
     for _ in range(args.steps):
@@ -147,8 +147,10 @@ def main():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-n", type=int, default=16)
+    ap.add_argument("--ref-n", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="cells per direction (profiling runs only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -164,7 +166,8 @@ def main():
 
     from paper_2602_13841_gb300 import build, inputs, stmg
     build.build()
-    w = WORKLOAD
+    w = dict(WORKLOAD)
+    w["n"] = args.n
     p = stmg.default_params(dim=w["d"], n_cells_1d=w["n"], r=w["r"], k=w["k"], nu=w["nu"], tau=w["tau"],
                             problem=w["problem"], precond_precision=stmg.STMG_FP32, newton_rtol=1e-10,
                             omega=0.3)
@@ -217,25 +220,27 @@ def main():
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     S.set_timing(False)
-    hV = torch.empty(Nv, dtype=torch.float64).pin_memory()
-    hU = torch.empty(Nst, dtype=torch.float64).pin_memory()
-    hV.copy_(V0.cpu())
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        for sl in range(args.steps):
-            Vp.copy_(hV, non_blocking=True)
-            S.initial_guess(Vp, U)
-            S.slab_solve(sl * w["tau"], Vp, U)
-            hU.copy_(U, non_blocking=True)
-            stream.synchronize()
-            hV.copy_(hU[k * Nv:(k + 1) * Nv])
-        e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_e2e = e0.elapsed_time(e1)
-    e2e = {"value": ws * Nst * args.steps / (ms_e2e * 1e-3), "unit": "DoF/s",
-           "h2d_bytes_per_step": Nv * 8, "d2h_bytes_per_step": Nst * 8}
+    e2e = None
+    if not args.no_e2e:
+        hV = torch.empty(Nv, dtype=torch.float64).pin_memory()
+        hU = torch.empty(Nst, dtype=torch.float64).pin_memory()
+        hV.copy_(V0.cpu())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for sl in range(args.steps):
+                Vp.copy_(hV, non_blocking=True)
+                S.initial_guess(Vp, U)
+                S.slab_solve(sl * w["tau"], Vp, U)
+                hU.copy_(U, non_blocking=True)
+                stream.synchronize()
+                hV.copy_(hU[k * Nv:(k + 1) * Nv])
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_e2e = e0.elapsed_time(e1)
+        e2e = {"value": ws * Nst * args.steps / (ms_e2e * 1e-3), "unit": "DoF/s",
+               "h2d_bytes_per_step": Nv * 8, "d2h_bytes_per_step": Nst * 8}
 
     # ---- roofline of the dominant kernel (Vanka patch apply, HBM-bound) from the live timers
     prof = S.kernel_profile()
@@ -246,7 +251,7 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            v, dt, nst, desc = oracle_sample(n=16)
+            v, dt, nst, desc = oracle_sample(n=8)
             cpu = {"value": v, "unit": "DoF/s", "cores": _cpu_cores(), "kind": "oracle", "sample": desc}
         line = {
             "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps,

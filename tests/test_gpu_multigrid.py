@@ -115,7 +115,7 @@ def test_smoother_and_vcycle_match_oracle(d, n, r, k, amp, prec):
 def test_slab_solve_reaches_tolerance_and_matches_exact_solution(precision, d, n, r, k, amp, nu, tau, pname):
     import torch
     S, mg, verts = _setup(d, n, r, k, amp, precision=precision, nu=nu, tau=tau, problem=pname,
-                          newton_rtol=1e-10)
+                          newton_rtol=1e-10, newton_atol=0.0)
     L0 = mg.levels[0]
     prob = problems.make(pname, nu)
     V0 = torch.empty(L0.lay.Nv, dtype=torch.float64, device="cuda")

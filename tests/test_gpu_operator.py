@@ -115,7 +115,8 @@ def test_every_level_of_the_hierarchy_matches_oracle():
         td = TimeData(L["k"], S.params.tau)
         U = inputs.uniform(L["Nst"], 20 + lvl)
         x = inputs.uniform(L["Nst"], 40 + lvl)
-        y_or = forms.jacobian(sp, td, U, S.params.nu) @ x
+        hscale = (L["n"] / n) / ((r + 1) * (r + 2))        # every level keeps the finest penalty
+        y_or = forms.jacobian(sp, td, U, S.params.nu, hscale=hscale) @ x
         y = torch.empty(L["Nst"], dtype=torch.float64, device="cuda")
         S.apply(_t(U), _t(x), y, lvl, stmg.STMG_FP64)
         torch.cuda.synchronize()
