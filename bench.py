@@ -34,7 +34,12 @@ if ROOT not in sys.path:
 METRIC = "ST operator apply GDoF/s; Newton-GMRES slab-solve time; serving p50/p99 latency"
 WORKLOAD = dict(d=2, n=256, r=2, k=2, amp=0.1, seed=1234, nu=1e-3, tau=0.05, problem="TG2D")
 WORKLOAD_NAME = ("2D unit square 256x256 mapped (amp 0.1h, seed 1234), Q3/P2disc (r=2), DG(2), "
-                 "dt=0.05, Re=1000 Taylor-Green; FP32 hp-STMG in FP64 Newton-FGMRES, rtol 1e-10")
+                 "dt=0.05, Re=1000 Taylor-Green; FP32 hp-STMG in FP64 Newton-FGMRES, "
+                 "||R||_M <= max(1e-10 ||R_0||_M, 1e-14)")
+# Absolute floor of the Newton test in the mass-weighted norm.  The Newton guess (the previous
+# slab's end value at every time node) makes ||R_0||_M ~ 1.8e-8 on this workload, so 1e-10
+# relative alone would ask for 1.8e-18, below what the FP64 residual resolves.
+ATOL = 1e-14
 
 
 def _dist():
@@ -104,7 +109,7 @@ def oracle_sample(n=16, slabs=1):
     w = WORKLOAD
     prob = problems.make(w["problem"], w["nu"])
     verts = inputs.vertices(w["d"], n, w["amp"], w["seed"])
-    S = krylov.SlabSolver(w["d"], n, w["r"], w["k"], verts, w["tau"], prob, omega=0.3, rtol=1e-10)
+    S = krylov.SlabSolver(w["d"], n, w["r"], w["k"], verts, w["tau"], prob, omega=0.3, rtol=1e-10, atol=ATOL)
     L = S.L
     Vprev = forms.interpolate_velocity(L.space, prob.v0)
     t = time.perf_counter()
@@ -170,7 +175,7 @@ def main():
     w["n"] = args.n
     p = stmg.default_params(dim=w["d"], n_cells_1d=w["n"], r=w["r"], k=w["k"], nu=w["nu"], tau=w["tau"],
                             problem=w["problem"], precond_precision=stmg.STMG_FP32, newton_rtol=1e-10,
-                            omega=0.3)
+                            newton_atol=ATOL, omega=0.3)
     stream = torch.cuda.Stream(device=dev)
     S = stmg.Solver(p, inputs.vertices(w["d"], w["n"], w["amp"], w["seed"]), stream=stream.cuda_stream)
     L = S.levels[0]

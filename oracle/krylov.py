@@ -172,7 +172,7 @@ def newton_slab(U0, Vprev, t0, residual, jac_apply, mnorm, mdot, mg, prm, stats=
 
 DEFAULTS = dict(rtol=1e-8, atol=1e-12, maxit=20, ew_eta0=0.4, ew_c=0.5, ew_theta=1.5, ew_min=1e-3,
                 ew_max=0.8, ls_lambda0=1.0, ls_c=1e-4, ls_tau=0.5, ls_alpha_min=1e-3, ls_maxbt=5,
-                ls_window=5, restart=30, gmres_maxit=50, thetaN=1.0, thetaL=2.0, kappa_abs=50,
+                ls_window=5, restart=50, gmres_maxit=50, thetaN=1.0, thetaL=2.0, kappa_abs=50,
                 stag_s=3, stag_theta=0.95)
 
 

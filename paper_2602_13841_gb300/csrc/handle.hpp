@@ -48,14 +48,26 @@ struct Handle {
   int* flag = nullptr;
   bool solver_ready = false;
   bool timing = false;
-  PhaseTimer t_rebuild, t_vanka, t_mg, t_outer;
+  PhaseTimer t_rebuild, t_mg;
   // per kernel class (KernelClass) device time, launch count and algorithmic bytes, timing mode
   PhaseTimer kt[8];
   long long kcount[8] = {};
   double kbytes[8] = {};
-  void kbegin(int cls) { if (timing) kt[cls].begin(stream); }
+  // While a CUDA graph is being captured, timer spans get their own events (graph event-record
+  // nodes) and go to `capsink`; they are read after every replay of that graph.
+  std::vector<CapSpan>* capsink = nullptr;
+  cudaEvent_t cap_open[8] = {};
+  void kbegin(int cls) {
+    if (!timing) return;
+    if (capsink) { cudaEventCreate(&cap_open[cls]); cudaEventRecord(cap_open[cls], stream); }
+    else kt[cls].begin(stream);
+  }
   void kend(int cls, double bytes = 0.0, int launches = 1) {
-    if (timing) { kt[cls].end(stream); kcount[cls] += launches; kbytes[cls] += bytes; }
+    if (!timing) return;
+    if (capsink) {
+      cudaEvent_t e; cudaEventCreate(&e); cudaEventRecord(e, stream);
+      capsink->push_back({cls, cap_open[cls], e, bytes, launches});
+    } else { kt[cls].end(stream); kcount[cls] += launches; kbytes[cls] += bytes; }
   }
   ~Handle();
   void* dalloc(size_t bytes);          // cudaMalloc tracked for release; throws std::bad_alloc

@@ -138,7 +138,6 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
       CKE(vaxpby<T>(lv.Nst, (T)1, rhs, (T)-1, q[l], s));
       res = q[l];
     }
-    if (h->timing) h->t_vanka.begin(s);
     const double m = (double)vanka_patch_size(lv);
     for (int c = 0; c < lv.ncolors; ++c) {
       // algorithmic bytes: the patch inverses of the colour's cells, residual gather, d update
@@ -146,7 +145,6 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
       CKE(vanka_apply<T>(lv, h->pb, inv[l], res, d, omega, c, s));
       h->kend(KC_VANKA_APPLY, (double)lv.colors[c].count * (m * m + 3.0 * m) * sizeof(T));
     }
-    if (h->timing) h->t_vanka.end(s);
   }
   return cudaSuccess;
 }
@@ -175,6 +173,54 @@ cudaError_t MG<T>::vcycle_level(int l, const T* rhs, T* d) {
 template <typename T>
 cudaError_t MG<T>::vcycle(const T* rhs, T* zz) {
   return vcycle_level(0, rhs, zz);
+}
+
+template <typename T>
+void MG<T>::drop_graph() {
+  if (graph_exec) cudaGraphExecDestroy(graph_exec);
+  if (graph) cudaGraphDestroy(graph);
+  graph_exec = nullptr;
+  graph = nullptr;
+  for (auto& sp : gspans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
+  gspans.clear();
+}
+
+template <typename T>
+cudaError_t MG<T>::vcycle_graph() {
+  cudaStream_t s = h->stream;
+  if (graph_exec && graph_timing != h->timing) drop_graph();
+  if (!graph_exec) {
+    // capture the V-cycle on r[0] -> z[0]; all buffers and parameters are fixed per handle, so
+    // the graph stays valid across smoother rebuilds
+    gspans.clear();
+    if (h->timing) h->capsink = &gspans;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { h->capsink = nullptr; return e; }
+    cudaError_t ev = vcycle_level(0, r[0], z[0]);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    h->capsink = nullptr;
+    if (ev != cudaSuccess) { if (g) cudaGraphDestroy(g); return ev; }
+    if (e != cudaSuccess) return e;
+    graph = g;
+    CKE(cudaGraphInstantiate(&graph_exec, graph, 0));
+    graph_timing = h->timing;
+  }
+  return cudaGraphLaunch(graph_exec, s);
+}
+
+template <typename T>
+void MG<T>::collect_graph_timers() {
+  for (auto& sp : gspans) {
+    float m = 0;
+    if (cudaEventElapsedTime(&m, sp.a, sp.b) == cudaSuccess) {
+      h->kt[sp.cls].ms += m;
+      h->kcount[sp.cls] += sp.launches;
+      h->kbytes[sp.cls] += sp.bytes;
+    } else {
+      cudaGetLastError();
+    }
+  }
 }
 
 template struct MG<float>;

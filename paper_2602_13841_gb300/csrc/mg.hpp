@@ -12,6 +12,10 @@ namespace stmg {
 
 struct Handle;
 
+// A timer span (kernel class, begin / end events, algorithmic bytes, launches) recorded inside
+// a captured CUDA graph.
+struct CapSpan { int cls; cudaEvent_t a, b; double bytes; int launches; };
+
 template <typename T>
 struct MG {
   Handle* h = nullptr;
@@ -30,6 +34,17 @@ struct MG {
   int* gj_piv = nullptr;
   bool built = false;
   bool smoothable = true;            // every smoothed level's patch fits on-chip memory
+  // The V-cycle of one smoother build is a fixed launch sequence on fixed buffers: it is
+  // captured once into a CUDA graph and replayed (launch overhead of the ~40 small launches per
+  // level).  Timer spans recorded during the capture are re-read after every replay.
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  bool use_graph = true;
+  bool graph_timing = false;         // the captured graph contains timer event nodes
+  std::vector<CapSpan> gspans;       // timer spans inside the captured graph
+  void drop_graph();
+  cudaError_t vcycle_graph();        // z[0] = B^{-1} r[0] through the captured graph
+  void collect_graph_timers();       // after a stream synchronisation following a replay
 
   cudaError_t allocate(Handle* h);
   // Level states from the fine FP64 slab state, patch inverses on every smoothed level,

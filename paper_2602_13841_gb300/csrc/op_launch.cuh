@@ -2,6 +2,7 @@
 #pragma once
 #include "level.hpp"
 #include "operator.cuh"
+#include "operator2d.cuh"
 #include "counters.hpp"
 
 namespace stmg {
@@ -59,8 +60,14 @@ static cudaError_t launch_dn(const Level& lv, const Problem& pb, double t0, cons
   for (int c = 0; c < lv.ncolors; ++c) {
     const ColorInfo& ci = lv.colors[c];
     if (ci.count > 0) {
-      dim3 grid((ci.count + cpb - 1) / cpb, batch);
-      k_volume<T, D, N, MODE><<<grid, cpb * Q, smem, stream>>>(A, tb, ci, cpb);
+      if constexpr (D == 2) {
+        constexpr int cpw = 32 / Q, per_block = 8 * cpw;
+        dim3 grid((ci.count + per_block - 1) / per_block, batch);
+        k_volume2d<T, N, MODE><<<grid, 256, 0, stream>>>(A, tb, ci);
+      } else {
+        dim3 grid((ci.count + cpb - 1) / cpb, batch);
+        k_volume<T, D, N, MODE><<<grid, cpb * Q, smem, stream>>>(A, tb, ci, cpb);
+      }
       note_launch();
     }
     if (MODE != MM && lv.nbcells[c] > 0) {

@@ -121,7 +121,7 @@ void stmg_params_default(stmg_params* p) {
   p->ew_eta0 = 0.4; p->ew_c = 0.5; p->ew_theta = 1.5; p->ew_min = 1e-3; p->ew_max = 0.8;
   p->ls_lambda0 = 1.0; p->ls_c = 1e-4; p->ls_tau = 0.5; p->ls_alpha_min = 1e-3;
   p->ls_maxbt = 5; p->ls_window = 5;
-  p->gmres_restart = 30; p->gmres_maxit = 50;
+  p->gmres_restart = 50; p->gmres_maxit = 50;
   p->rebuild_thetaN = 1.0; p->rebuild_thetaL = 2.0; p->rebuild_kappa_abs = 50;
   p->stag_s = 3; p->stag_theta = 0.95;
 }

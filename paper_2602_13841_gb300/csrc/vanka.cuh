@@ -274,9 +274,21 @@ __device__ bool gauss_jordan(T* S, int m, int ld, int* piv_row, T* colbuf) {
     __syncthreads();
     for (int i = tid; i < m; i += nt) if (i != p) S[i * ld + p] = 0;
     __syncthreads();
-    for (int e = tid; e < m * m; e += nt) {
-      const int i = e / m, j = e % m;
-      if (i != p) S[i * ld + j] -= colbuf[i] * S[p * ld + j];
+    // elimination: thread owns column j and every `rs`-th row (no division in the loop)
+    if (nt >= m) {
+      const int rs = nt / m;
+      if (tid < rs * m) {
+        const int j = tid % m, chunk = tid / m;
+        const T prow = S[p * ld + j];
+        for (int i = chunk; i < m; i += rs)
+          if (i != p) S[i * ld + j] -= colbuf[i] * prow;
+      }
+    } else {
+      for (int j = tid; j < m; j += nt) {
+        const T prow = S[p * ld + j];
+        for (int i = 0; i < m; ++i)
+          if (i != p) S[i * ld + j] -= colbuf[i] * prow;
+      }
     }
     __syncthreads();
   }
@@ -416,9 +428,18 @@ __global__ void k_vanka_apply(LevelArgs<T> L, const T* __restrict__ inv, const T
   __syncthreads();
   const T* Sinv = inv + cell * (int64_t)m * m;
   for (int i = tid; i < m; i += nt) {
-    T acc = 0;
-    for (int j = 0; j < m; ++j) acc += Sinv[(int64_t)j * m + i] * r[j];
-    d[gidx[i]] += omega * acc;
+    // four independent accumulators keep several column loads in flight per thread
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    const T* col = Sinv + i;
+    int j = 0;
+    for (; j + 3 < m; j += 4) {
+      a0 += __ldg(col + (int64_t)j * m) * r[j];
+      a1 += __ldg(col + (int64_t)(j + 1) * m) * r[j + 1];
+      a2 += __ldg(col + (int64_t)(j + 2) * m) * r[j + 2];
+      a3 += __ldg(col + (int64_t)(j + 3) * m) * r[j + 3];
+    }
+    for (; j < m; ++j) a0 += __ldg(col + (int64_t)j * m) * r[j];
+    d[gidx[i]] += omega * ((a0 + a1) + (a2 + a3));
   }
 }
 
