@@ -156,6 +156,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="cells per direction (profiling runs only)")
+    ap.add_argument("--serving-requests", type=int, default=16,
+                    help="requests of the serving leg (Poisson stream, 20/s); 0 skips it")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -216,12 +218,8 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     launches = lib.stmg_launch_count() - launches0
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * Nst * args.steps / (ms * 1e-3)
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), ws, dev)
+    value = replica_throughput(ws, Nst, args.steps, ms)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     S.set_timing(False)
@@ -252,6 +250,23 @@ def main():
     roof = roofline(S, prof)
     buckets = {key: float(np.sum([st[key] for st in stats])) for key in ("t_rebuild", "t_vanka", "t_mg_other", "t_other")}
     peaks = _peaks()
+    S.close()
+    serving = None
+    if args.serving_requests > 0:
+        from paper_2602_13841_gb300 import serving as srv
+        # the serving workload's distribution restricted to the shapes whose Vanka patches fit
+        # on-chip memory (3D: r = 1, k <= 1); seeded Poisson arrivals at 20 requests per second
+        reqs = srv.poisson_stream(args.serving_requests, 20.0, 7, orders=(1, 2, 3), ks=(0, 1, 2))
+        for q in reqs:
+            if q.d == 3:
+                q.r, q.k = 1, min(q.k, 1)
+        server = srv.Server(workers=4)
+        res = server.run(reqs, realtime=True)
+        server.close()
+        serving = srv.report(res)
+        serving["workers"] = 4
+        serving["stream"] = ("Poisson 20/s seed 7; 2D n in {16..256}, 3D n in {8..48}, r in {1,2,3} (3D r=1), "
+                             "k in {0,1,2} (3D k<=1), Re ~ U[100,2000]; one slab each")
 
     if rank == 0:
         cpu = None
@@ -271,11 +286,26 @@ def main():
                        "gmres_its": [st["gmres_its_total"] for st in stats],
                        "rebuilds": [st["rebuilds"] for st in stats],
                        "res_ratio": [st["res_final"] / st["res0"] for st in stats]},
-            "phase_seconds": buckets, "kernels": prof, "peaks": peaks,
+            "phase_seconds": buckets, "kernels": prof, "peaks": peaks, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def max_over_ranks(ms, ws, device):
+    """The slowest rank's timed region (all ranks take part; single rank: unchanged)."""
+    if ws <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(ws, nst, steps, ms):
+    """Whole-job DoF/s: every rank solves `steps` slabs of nst DoFs (independent replicas)."""
+    return ws * nst * steps / (ms * 1e-3)
 
 
 def _peaks():

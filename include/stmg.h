@@ -74,6 +74,7 @@ typedef struct {
   int gmres_restart, gmres_maxit;                               /* 30, 50 */
   double rebuild_thetaN, rebuild_thetaL; int rebuild_kappa_abs; /* Alg. 1 rebuild triggers */
   int stag_s; double stag_theta;                                /* FGMRES stagnation window */
+  double omega_p;      /* Vanka relaxation of the pressure DoFs (velocity DoFs use omega) */
 } stmg_params;
 
 /* Fill *p with the paper's defaults (Sec. 5, Alg. 1-2) for a d-dimensional problem. */
@@ -88,6 +89,16 @@ void stmg_params_default(stmg_params* p);
 stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_stream stream,
                         stmg_handle** out);
 void stmg_destroy(stmg_handle* h);
+
+/* Device bytes a handle with these parameters needs once its slab solver is set up (mesh
+ * hierarchy, level vectors, Vanka patch inverses, transfer and coarse work space, FGMRES basis),
+ * computed without allocating: the admission test of the serving loop. */
+stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes);
+
+/* Change viscosity, slab length and analytic data of an existing handle; the mesh hierarchy
+ * and all device work space stay resident (serving requests of one shape reuse a handle).
+ * The next slab solve rebuilds the smoother. */
+stmg_status stmg_set_physics(stmg_handle* h, double nu, double tau, int problem);
 const char* stmg_last_error(const stmg_handle* h);
 
 /* Number of levels of the hp hierarchy (level 0 = finest) and the sizes of one level. */

@@ -190,8 +190,13 @@ def patch_dofs(level, cell):
 class Vanka:
     """Cell-wise space-time Vanka with midpoint-surrogate patch matrices (Sec. 4.3)."""
 
-    def __init__(self, level, U, omega):
+    def __init__(self, level, U, omega, omega_p=None):
         self.level, self.omega = level, omega
+        self.omega_p = omega if omega_p is None else omega_p
+        nv = (level.k + 1) * level.lay.Nv
+        # relaxation per DoF: omega on the (overlapping) velocity DoFs, omega_p on the pressure
+        # DoFs, each of which belongs to exactly one patch
+        self.weights = np.where(np.arange(level.Nst) < nv, omega, self.omega_p)
         vstar = midpoint_velocity(level, U)
         Jt = forms.jacobian(level.space, level.td, U, level.nu, *level.gamma, level.bconv, vstar=vstar,
                             hscale=level.hscale)
@@ -203,12 +208,13 @@ class Vanka:
             self.patches.append((idx, sla.lu_factor(S)))
 
     def sweep(self, J, rhs, d):
-        """d <- d + omega sum_K R_K^T S~_K^{-1} R_K (rhs - J d) (Eq. vanka0)."""
+        """d <- d + W sum_K R_K^T S~_K^{-1} R_K (rhs - J d) (Eq. vanka0); W = omega on velocity
+        DoFs, omega_p on pressure DoFs (W = omega I when omega_p = omega)."""
         res = rhs - J @ d
         upd = np.zeros_like(d)
         for idx, lu in self.patches:
             upd[idx] += sla.lu_solve(lu, res[idx])
-        return d + self.omega * upd
+        return d + self.weights * upd
 
 
 class CoarseSolver:
@@ -235,7 +241,7 @@ class CoarseSolver:
 class Multigrid:
     """hp-STMG V-cycle: z = B^{-1} r on the finest level (Sec. 4.2)."""
 
-    def __init__(self, d, n, r, k, vertices, tau, nu, omega=0.7, nu1=1, nu2=1,
+    def __init__(self, d, n, r, k, vertices, tau, nu, omega=0.3, nu1=1, nu2=1, omega_p=1.0,
                  gamma=(10.0, 10.0), bconv=True, max_h=-1):
         p0 = r + 1
         self.levels = [Level(d, ln, lr, lk, lv, tau, nu, gamma, bconv, hscale=(ln / n) / (p0 * (p0 + 1)))
@@ -245,7 +251,7 @@ class Multigrid:
             P, I = transfer(f, c)
             self.P.append(P)
             self.I.append(I)
-        self.omega, self.nu1, self.nu2 = omega, nu1, nu2
+        self.omega, self.omega_p, self.nu1, self.nu2 = omega, omega_p, nu1, nu2
 
     def level_states(self, U):
         """Velocity state of every level (pressure entries zero) from the fine slab vector."""
@@ -262,7 +268,7 @@ class Multigrid:
         self.states = self.level_states(U)
         self.J = [forms.jacobian(L.space, L.td, S, L.nu, *L.gamma, L.bconv, hscale=L.hscale)
                   for L, S in zip(self.levels, self.states)]
-        self.smoothers = [Vanka(L, S, self.omega) for L, S in zip(self.levels[:-1], self.states[:-1])]
+        self.smoothers = [Vanka(L, S, self.omega, self.omega_p) for L, S in zip(self.levels[:-1], self.states[:-1])]
         self.coarse = CoarseSolver(self.levels[-1], self.J[-1])
 
     def vcycle(self, r, l=0):

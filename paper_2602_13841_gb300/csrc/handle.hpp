@@ -59,13 +59,14 @@ struct Handle {
   cudaEvent_t cap_open[8] = {};
   void kbegin(int cls) {
     if (!timing) return;
-    if (capsink) { cudaEventCreate(&cap_open[cls]); cudaEventRecord(cap_open[cls], stream); }
+    // external event-record nodes: the graph records these events at every replay
+    if (capsink) { cudaEventCreate(&cap_open[cls]); cudaEventRecordWithFlags(cap_open[cls], stream, cudaEventRecordExternal); }
     else kt[cls].begin(stream);
   }
   void kend(int cls, double bytes = 0.0, int launches = 1) {
     if (!timing) return;
     if (capsink) {
-      cudaEvent_t e; cudaEventCreate(&e); cudaEventRecord(e, stream);
+      cudaEvent_t e; cudaEventCreate(&e); cudaEventRecordWithFlags(e, stream, cudaEventRecordExternal);
       capsink->push_back({cls, cap_open[cls], e, bytes, launches});
     } else { kt[cls].end(stream); kcount[cls] += launches; kbytes[cls] += bytes; }
   }

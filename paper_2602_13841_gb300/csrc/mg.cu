@@ -142,7 +142,7 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
     for (int c = 0; c < lv.ncolors; ++c) {
       // algorithmic bytes: the patch inverses of the colour's cells, residual gather, d update
       h->kbegin(KC_VANKA_APPLY);
-      CKE(vanka_apply<T>(lv, h->pb, inv[l], res, d, omega, c, s));
+      CKE(vanka_apply<T>(lv, h->pb, inv[l], res, d, omega, h->prm.omega_p, c, s));
       h->kend(KC_VANKA_APPLY, (double)lv.colors[c].count * (m * m + 3.0 * m) * sizeof(T));
     }
   }

@@ -64,7 +64,7 @@ cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar
                         T* inv, int* status, cudaStream_t s);
 template <typename T>
 cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const T* res, T* d, double omega,
-                        int color, cudaStream_t s);
+                        double omega_p, int color, cudaStream_t s);
 size_t vanka_patch_size(const Level& lv);            // m_st
 size_t vanka_elem_size(const Level& lv, int which);  // entries per cell of EA (0), EB (1), EM (2)
 bool vanka_supported(const Level& lv, size_t esize);

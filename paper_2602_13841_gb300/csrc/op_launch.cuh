@@ -70,7 +70,7 @@ static cudaError_t launch_dn(const Level& lv, const Problem& pb, double t0, cons
       }
       note_launch();
     }
-    if (MODE != MM && lv.nbcells[c] > 0) {
+    if (D == 3 && MODE != MM && lv.nbcells[c] > 0) {       // 2D: faces fused into k_volume2d
       dim3 grid((lv.nbcells[c] + fcpb - 1) / fcpb, batch);
       k_faces<T, D, N, MODE><<<grid, fcpb * Q, fsmem, stream>>>(A, tb, lv.bcells[c], lv.nbcells[c], fcpb);
       note_launch();

@@ -12,6 +12,8 @@
 
 namespace stmg {
 
+constexpr int MAXNP2D = 10;   // C(r+2, 2) for r <= 3
+
 template <typename T, int N>
 __device__ __forceinline__ T shfl_x(T v, const T (*M)[MAXN], int row, int base, bool transpose) {
   // sum_j M[row][j] v(lane base + j)   (or M[j][row] when transposed); base = cell row start
@@ -34,6 +36,159 @@ __device__ __forceinline__ T shfl_y(T v, const T (*M)[MAXN], int row, int base, 
     acc += (transpose ? M[j][row] : M[row][j]) * o;
   }
   return acc;
+}
+
+// Boundary-face terms of one face (axis, side) for time node a, added to the node outputs
+// out[c] of lane (tx, ty) and to the pressure output pout of lane t = m (mode m).  Same
+// integrand as k_faces (operator.cuh).  Face point p of face axis 0 is held by every lane of row
+// ty = p (face axis 1: column tx = p); values at the face come from the GLL end-node row /
+// column (L_j(side) = delta) followed by a 1D interpolation along the face; the normal reference
+// derivative uses Dend.  All lanes of the warp execute this (shuffles), contributions of cells
+// without this face are masked by `has`.
+template <typename T, int N, int MODE>
+__device__ __forceinline__ void face2d(const OpArgs<T>& A, const Tab<T>& tb, int a, int axis, int side, bool has,
+                                       const T (*corner)[3], const int* cc, int64_t gnode, int64_t cell, int tx,
+                                       int ty, int t, int cb, T vol, T* out, T& pout) {
+  constexpr bool RES = (MODE == MR);
+  const LevelArgs<T>& L = A.L;
+  const int kp1 = tb.k + 1, npc = tb.npc;
+  const int e = side * (N - 1);
+  const int tn = axis == 0 ? tx : ty;           // lane index along the normal direction
+  const int tt = axis == 0 ? ty : tx;           // lane index along the face (= face point p)
+  // nodal values of the increment and of the state at this lane's node (time node a)
+  T u[2] = {0, 0}, s[2] = {0, 0};
+  if (has)
+    for (int c = 0; c < 2; ++c) {
+      const int64_t gi = (int64_t)a * L.Nv + c * L.nnodes + gnode;
+      u[c] = A.x[gi];
+      s[c] = (MODE == MJ) ? A.state[gi] : u[c];
+    }
+  const T pma = (has && t < npc) ? A.x[(int64_t)kp1 * L.Nv + (int64_t)a * L.Np + cell * npc + t] : (T)0;
+  // end-node value and normal reference derivative on every lane of the face-parallel line
+  T fv[2], fs[2], fdn[2], fdt[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    T ve, vd, se;
+    if (axis == 0) {
+      ve = __shfl_sync(0xffffffffu, u[c], cb + ty * N + e);
+      se = __shfl_sync(0xffffffffu, s[c], cb + ty * N + e);
+      T acc = 0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc += tb.Dend[side][j] * __shfl_sync(0xffffffffu, u[c], cb + ty * N + j);
+      vd = acc;
+      // interpolate along y to face point p = ty
+      fv[c] = shfl_y<T, N>(ve, tb.B, ty, cb + tx, false);
+      fs[c] = shfl_y<T, N>(se, tb.B, ty, cb + tx, false);
+      fdn[c] = shfl_y<T, N>(vd, tb.B, ty, cb + tx, false);
+      fdt[c] = shfl_y<T, N>(ve, tb.D, ty, cb + tx, false);
+    } else {
+      ve = __shfl_sync(0xffffffffu, u[c], cb + e * N + tx);
+      se = __shfl_sync(0xffffffffu, s[c], cb + e * N + tx);
+      T acc = 0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc += tb.Dend[side][j] * __shfl_sync(0xffffffffu, u[c], cb + j * N + tx);
+      vd = acc;
+      fv[c] = shfl_x<T, N>(ve, tb.B, tx, cb + ty * N, false);
+      fs[c] = shfl_x<T, N>(se, tb.B, tx, cb + ty * N, false);
+      fdn[c] = shfl_x<T, N>(vd, tb.B, tx, cb + ty * N, false);
+      fdt[c] = shfl_x<T, N>(ve, tb.D, tx, cb + ty * N, false);
+    }
+  }
+  // pressure at face point tt: psi_m(face point) = Pend[side][m_axis] P1[tt][m_other]
+  T fp = 0;
+#pragma unroll
+  for (int m = 0; m < MAXNP2D; ++m) {
+    if (m < npc) {
+      const T pm = __shfl_sync(0xffffffffu, pma, cb + m);
+      const T psi = (axis == 0) ? tb.Pend[side][tb.modes[m][0]] * tb.P1[tt][tb.modes[m][1]]
+                                : tb.P1[tt][tb.modes[m][0]] * tb.Pend[side][tb.modes[m][1]];
+      fp += psi * pm;
+    }
+  }
+  // geometry at the face point
+  T xh[3], J[3][3], G[3][3], xf[3];
+  xh[axis] = (T)side;
+  xh[1 - axis] = tb.qx[tt];
+  xh[2] = 0;
+  map_jacobian<T, 2>(corner, xh, J, xf);
+  const T det = invert<T, 2>(J, G);
+  const T nh = side ? (T)1 : (T)-1;
+  T nrm[2], len2 = 0;
+  for (int i = 0; i < 2; ++i) { nrm[i] = det * G[axis][i] * nh; len2 += nrm[i] * nrm[i]; }
+  const T dS = sqrt(len2);
+  nrm[0] /= dS; nrm[1] /= dS;
+  const T JxWf = dS * tb.qw[tt];
+  // face area (sum over the face points held by the lanes of one normal-direction column)
+  T area = 0;
+#pragma unroll
+  for (int p = 0; p < N; ++p) area += __shfl_sync(0xffffffffu, JxWf, axis == 0 ? cb + p * N : cb + p);
+  const T h = vol / area * L.hscale;
+  // physical gradient of the increment and normal derivatives
+  T dn[2];
+  T ghat[2];
+  for (int m = 0; m < 2; ++m) ghat[m] = G[m][0] * nrm[0] + G[m][1] * nrm[1];
+  for (int c = 0; c < 2; ++c) {
+    T gr[2];
+    gr[axis] = fdn[c];
+    gr[1 - axis] = fdt[c];
+    T g0 = G[0][0] * gr[0] + G[1][0] * gr[1], g1 = G[0][1] * gr[0] + G[1][1] * gr[1];
+    dn[c] = g0 * nrm[0] + g1 * nrm[1];
+  }
+  T y = fs[0] * nrm[0] + fs[1] * nrm[1];
+  const T ypos = (T)0.5 * (fabs(y) + y), yneg = (T)0.5 * (fabs(y) - y);
+  const T sgn = (y > 0) ? (T)1 : ((y < 0) ? (T)-1 : (T)0);
+  T ev[2], gd[2] = {0, 0};
+  if (RES) {
+    double xd[3] = {(double)xf[0], (double)xf[1], 0.0}, gv[3];
+    const double ta = (double)L.t0 + 0.5 * (double)L.tau * ((double)tb.that[a] + 1.0);
+    problem_g<2>(L.problem, xd, ta, (double)L.nu, gv);
+    gd[0] = (T)gv[0]; gd[1] = (T)gv[1];
+    ev[0] = fs[0] - gd[0]; ev[1] = fs[1] - gd[1];
+  } else {
+    ev[0] = fv[0]; ev[1] = fv[1];
+  }
+  const T en = ev[0] * nrm[0] + ev[1] * nrm[1];
+  const T gn = gd[0] * nrm[0] + gd[1] * nrm[1];
+  const T wJ = has ? tb.w[a] * JxWf : (T)0;
+  T ac[2], bg[2][2];
+  for (int c = 0; c < 2; ++c) {
+    T v = -L.nu * dn[c] + L.nu * L.gamma1 / h * ev[c] + L.gamma2 / h * en * nrm[c] + fp * nrm[c];
+    if (L.bconv) {
+      if (RES) v += (ypos - 2 * yneg) * fs[c] + (T)0.5 * (fabs(gn) - gn) * gd[c];
+      else v += (ypos - 2 * yneg) * fv[c] + (T)0.5 * ((T)3 - sgn) * en * fs[c];
+    }
+    ac[c] = wJ * v;
+    const T bc = -wJ * L.nu * ev[c];
+    bg[c][0] = bc * ghat[0];
+    bg[c][1] = bc * ghat[1];
+  }
+  const T sp = wJ * en;
+  // test functions: node (tx, ty) gets
+  //   [tn == e] (sum_p a(p) B[p][tt] + sum_p bg_t(p) D[p][tt]) + Dend[side][tn] sum_p bg_n(p) B[p][tt]
+  for (int c = 0; c < 2; ++c) {
+    T t1, t2, t3;
+    if (axis == 0) {
+      t1 = shfl_y<T, N>(ac[c], tb.B, ty, cb + tx, true);
+      t2 = shfl_y<T, N>(bg[c][1], tb.D, ty, cb + tx, true);
+      t3 = shfl_y<T, N>(bg[c][0], tb.B, ty, cb + tx, true);
+    } else {
+      t1 = shfl_x<T, N>(ac[c], tb.B, tx, cb + ty * N, true);
+      t2 = shfl_x<T, N>(bg[c][0], tb.D, tx, cb + ty * N, true);
+      t3 = shfl_x<T, N>(bg[c][1], tb.B, tx, cb + ty * N, true);
+    }
+    if (has) out[c] += (tn == e ? t1 + t2 : (T)0) + tb.Dend[side][tn] * t3;
+  }
+  // pressure test functions: lane m accumulates sum_p s(p) psi_m(p)
+  const int mo = t < npc ? t : 0;
+  T pa = 0;
+#pragma unroll
+  for (int p = 0; p < N; ++p) {
+    const T sv = __shfl_sync(0xffffffffu, sp, axis == 0 ? cb + p * N : cb + p);
+    const T psi = (axis == 0) ? tb.Pend[side][tb.modes[mo][0]] * tb.P1[p][tb.modes[mo][1]]
+                              : tb.P1[p][tb.modes[mo][0]] * tb.Pend[side][tb.modes[mo][1]];
+    pa += psi * sv;
+  }
+  if (has) pout += pa;
 }
 
 template <typename T, int N, int MODE>
@@ -113,10 +268,14 @@ __global__ void __launch_bounds__(256) k_volume2d(OpArgs<T> A, Tab<T> tb, ColorI
       T v = shfl_x<T, N>(vp[c], tb.B, tx, cb + ty * N, false);
       vp[c] = shfl_y<T, N>(v, tb.B, ty, cb + tx, false);
     }
-  // pressure basis at this quadrature point
-  T psi[MAXNP];
+  // cell volume |K| (for h_{Gamma_D} of boundary faces)
+  T vol = 0;
 #pragma unroll
-  for (int m = 0; m < MAXNP; ++m) psi[m] = (m < npc) ? tb.P1[tx][tb.modes[m][0]] * tb.P1[ty][tb.modes[m][1]] : (T)0;
+  for (int q = 0; q < Q; ++q) vol += __shfl_sync(0xffffffffu, JxW, cb + q);
+  // pressure basis at this quadrature point
+  T psi[MAXNP2D];
+#pragma unroll
+  for (int m = 0; m < MAXNP2D; ++m) psi[m] = (m < npc) ? tb.P1[tx][tb.modes[m][0]] * tb.P1[ty][tb.modes[m][1]] : (T)0;
 
   for (int a = 0; a < kp1; ++a) {
     // select time node a (registers are indexed statically)
@@ -136,7 +295,7 @@ __global__ void __launch_bounds__(256) k_volume2d(OpArgs<T> A, Tab<T> tb, ColorI
     }
     T pq = 0;
 #pragma unroll
-    for (int m = 0; m < MAXNP; ++m) {
+    for (int m = 0; m < MAXNP2D; ++m) {
       if (m < npc) pq += psi[m] * __shfl_sync(0xffffffffu, pma, cb + m);
     }
     T gp[2][2];
@@ -185,12 +344,12 @@ __global__ void __launch_bounds__(256) k_volume2d(OpArgs<T> A, Tab<T> tb, ColorI
       z[c] += shfl_x<T, N>(Fh[c][0], tb.Dc, tx, cb + ty * N, true);
       z[c] += shfl_y<T, N>(Fh[c][1], tb.Dc, ty, cb + tx, true);
     }
-    // quadrature -> nodes (transposed B passes) and scatter
+    // quadrature -> nodes (transposed B passes)
+    T vout[2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       T v = shfl_x<T, N>(z[c], tb.B, tx, cb + ty * N, true);
-      v = shfl_y<T, N>(v, tb.B, ty, cb + tx, true);
-      if (on) A.y[(int64_t)a * L.Nv + c * L.nnodes + gnode] += v;
+      vout[c] = shfl_y<T, N>(v, tb.B, ty, cb + tx, true);
     }
     // pressure test functions: lane cb + m accumulates sum_t psi_m(t) sp(t)
     T pacc = 0;
@@ -199,6 +358,20 @@ __global__ void __launch_bounds__(256) k_volume2d(OpArgs<T> A, Tab<T> tb, ColorI
     for (int q = 0; q < Q; ++q) {
       T s = __shfl_sync(0xffffffffu, sp, cb + q);
       pacc += tb.P1[q % N][tb.modes[mo][0]] * tb.P1[q / N][tb.modes[mo][1]] * s;
+    }
+    // boundary faces (Nitsche, boundary convection) of boundary cells
+    if (MODE != MM) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int axis = f >> 1, side = f & 1;
+        const bool has = on && (side == 0 ? cc[axis] == 0 : cc[axis] == L.n - 1);
+        if (__any_sync(0xffffffffu, has))
+          face2d<T, N, MODE>(A, tb, a, axis, side, has, corner, cc, gnode, cell, tx, ty, t, cb, vol, vout, pacc);
+      }
+    }
+    if (on) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) A.y[(int64_t)a * L.Nv + c * L.nnodes + gnode] += vout[c];
     }
     if (on && t < npc) A.y[poff + (int64_t)a * L.Np + cell * npc + t] += pacc;
   }

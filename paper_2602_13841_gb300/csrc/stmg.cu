@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+#include <array>
 #include <atomic>
 
 #include "../../include/stmg.h"
@@ -124,6 +126,61 @@ void stmg_params_default(stmg_params* p) {
   p->gmres_restart = 50; p->gmres_maxit = 50;
   p->rebuild_thetaN = 1.0; p->rebuild_thetaL = 2.0; p->rebuild_kappa_abs = 50;
   p->stag_s = 3; p->stag_theta = 0.95;
+  p->omega_p = 1.0;
+}
+
+stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
+  if (!p || !bytes) return STMG_ERR_ARG;
+  if (p->dim < 2 || p->dim > 3 || p->r < 1 || p->r > 3 || p->k < 0 || p->k > 2 || p->n_cells_1d < 1)
+    return STMG_ERR_ARG;
+  const int d = p->dim, n = p->n_cells_1d;
+  std::vector<std::array<int, 3>> lv;     // (n, r, k) of every level, same rule as stmg_create
+  int r = p->r, k = p->k;
+  lv.push_back({n, r, k});
+  while (height(r) > 0 || height(k) > 0) {
+    if (height(r) > height(k)) r /= 2;
+    else if (height(k) > height(r)) k /= 2;
+    else { r /= 2; k /= 2; }
+    lv.push_back({n, r, k});
+  }
+  int nn = n, hl = 0;
+  while (nn % 2 == 0 && nn / 2 >= 2 && (p->n_levels_h < 0 || hl < p->n_levels_h)) { nn /= 2; ++hl; lv.push_back({nn, r, k}); }
+  const double es = p->precond_precision == STMG_FP32 ? 4.0 : 8.0;
+  double tot = 0, ea = 0, eb = 0, em = 0, nvmax = 0;
+  std::vector<double> nst(lv.size());
+  for (size_t l = 0; l < lv.size(); ++l) {
+    const int ln = lv[l][0], lr = lv[l][1], lk = lv[l][2];
+    double N1 = (lr + 1.0) * ln + 1.0, nodes = std::pow(N1, d), cells = std::pow((double)ln, d);
+    double npc = (d == 2) ? (lr + 1.0) * (lr + 2.0) / 2.0 : (lr + 1.0) * (lr + 2.0) * (lr + 3.0) / 6.0;
+    double Nv = d * nodes, Np = cells * npc;
+    nst[l] = (lk + 1.0) * (Nv + Np);
+    tot += 12.0 * std::pow(ln + 1.0, d) + 4.0 * cells;                  // vertices, boundary lists
+    tot += 5.0 * nst[l] * es;                                            // level vectors
+    if (l + 1 < lv.size()) {
+      double nl = std::pow(lr + 2.0, d), mv = d * nl, m = (lk + 1.0) * (mv + npc);
+      tot += cells * m * m * es;                                         // patch inverses
+      ea = std::max(ea, cells * mv * mv); eb = std::max(eb, cells * npc * mv); em = std::max(em, cells * nl * nl);
+      nvmax = std::max(nvmax, Nv);
+      tot += 3.0 * std::max((lk + 1.0) * Nv, (lk + 1.0) * Np) * es;      // transfer scratch
+    }
+  }
+  tot += (ea + eb + em + nvmax) * es;
+  const double Nc = nst.back(), Nb = Nc + lv.back()[2] + 1;
+  tot += Nb * Nb * 12.0 + Nc * Nc * 8.0;                                 // coarse factors
+  tot += (2.0 * p->gmres_restart + 1.0 + 9.0) * nst[0] * 8.0;           // Krylov basis, Newton vectors
+  *bytes = (uint64_t)tot;
+  return STMG_OK;
+}
+
+stmg_status stmg_set_physics(stmg_handle* hh, double nu, double tau, int problem) {
+  if (!hh || !(nu > 0) || !(tau > 0) || problem < 0 || problem > 3) return STMG_ERR_ARG;
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  h->prm.nu = nu; h->prm.tau = tau; h->prm.problem = problem;
+  h->pb.nu = nu; h->pb.tau = tau; h->pb.problem = problem;
+  // the captured V-cycle bakes the physics into its kernel parameters
+  if (h->mg32) h->mg32->drop_graph();
+  if (h->mg64) h->mg64->drop_graph();
+  return STMG_OK;
 }
 
 stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_stream stream,

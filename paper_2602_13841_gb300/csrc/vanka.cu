@@ -94,7 +94,7 @@ cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar
 
 template <typename T, int D, int N>
 static cudaError_t apply_dn(const Level& lv, const Problem& pb, const T* inv, const T* res, T* d, double omega,
-                            int color, cudaStream_t s) {
+                            double omega_p, int color, cudaStream_t s) {
   const ColorInfo& ci = lv.colors[color];
   if (ci.count == 0) return cudaSuccess;
   const int m = (int)vanka_patch_size(lv);
@@ -102,16 +102,16 @@ static cudaError_t apply_dn(const Level& lv, const Problem& pb, const T* inv, co
   if (threads > 256) threads = 256;
   size_t smem = sizeof(T) * (((m + 1) & ~1)) + sizeof(int64_t) * m + 16;
   k_vanka_apply<T, D, N><<<ci.count, threads, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, res, d, (T)omega,
-                                                         lv.k + 1, lv.npc, ci);
+                                                         (T)omega_p, lv.k + 1, lv.npc, ci);
   note_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const T* res, T* d, double omega,
-                        int color, cudaStream_t s) {
+                        double omega_p, int color, cudaStream_t s) {
   const int N = lv.r + 2;
-#define STMG_A(DD, NN) return apply_dn<T, DD, NN>(lv, pb, inv, res, d, omega, color, s)
+#define STMG_A(DD, NN) return apply_dn<T, DD, NN>(lv, pb, inv, res, d, omega, omega_p, color, s)
   if (lv.d == 2) { if (N == 3) STMG_A(2, 3); if (N == 4) STMG_A(2, 4); if (N == 5) STMG_A(2, 5); }
   else { if (N == 3) STMG_A(3, 3); if (N == 4) STMG_A(3, 4); }
 #undef STMG_A
@@ -123,8 +123,8 @@ template cudaError_t vanka_build<float>(const Level&, const Problem&, const floa
 template cudaError_t vanka_build<double>(const Level&, const Problem&, const double*, double*, double*, double*,
                                          double*, double*, int*, cudaStream_t);
 template cudaError_t vanka_apply<float>(const Level&, const Problem&, const float*, const float*, float*, double,
-                                        int, cudaStream_t);
+                                        double, int, cudaStream_t);
 template cudaError_t vanka_apply<double>(const Level&, const Problem&, const double*, const double*, double*,
-                                         double, int, cudaStream_t);
+                                         double, double, int, cudaStream_t);
 
 }  // namespace stmg

@@ -399,7 +399,7 @@ __global__ void k_patch(VankaArgs<T> V, Tab<T> tb, int64_t ncells) {
 // d[patch] += omega * S~^{-1} res[patch] for the cells of one colour (one block per cell).
 template <typename T, int D, int N>
 __global__ void k_vanka_apply(LevelArgs<T> L, const T* __restrict__ inv, const T* __restrict__ res,
-                              T* __restrict__ d, T omega, int kp1, int npc, ColorInfo ci) {
+                              T* __restrict__ d, T omega, T omega_p, int kp1, int npc, ColorInfo ci) {
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int m = kp1 * (MV + npc);
@@ -439,7 +439,7 @@ __global__ void k_vanka_apply(LevelArgs<T> L, const T* __restrict__ inv, const T
       a3 += __ldg(col + (int64_t)(j + 3) * m) * r[j + 3];
     }
     for (; j < m; ++j) a0 += __ldg(col + (int64_t)j * m) * r[j];
-    d[gidx[i]] += omega * ((a0 + a1) + (a2 + a3));
+    d[gidx[i]] += (i < kp1 * MV ? omega : omega_p) * ((a0 + a1) + (a2 + a3));
   }
 }
 

@@ -38,6 +38,7 @@ class Params(ctypes.Structure):
         ("rebuild_thetaN", ctypes.c_double), ("rebuild_thetaL", ctypes.c_double),
         ("rebuild_kappa_abs", ctypes.c_int),
         ("stag_s", ctypes.c_int), ("stag_theta", ctypes.c_double),
+        ("omega_p", ctypes.c_double),
     ]
 
 
@@ -85,6 +86,8 @@ def load():
                                     ctypes.POINTER(ctypes.c_double)]),
         "stmg_kernel_profile_reset": (I, [P]),
         "stmg_launch_count": (ctypes.c_longlong, []),
+        "stmg_footprint": (I, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_uint64)]),
+        "stmg_set_physics": (I, [P, D, D, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -103,6 +106,16 @@ def default_params(**kw):
             val = PROBLEMS[val]
         setattr(p, key, val)
     return p
+
+
+def footprint(params):
+    """Device bytes a handle with these parameters needs for slab solves (no allocation)."""
+    lib = load()
+    b = ctypes.c_uint64()
+    st = lib.stmg_footprint(ctypes.byref(params), ctypes.byref(b))
+    if st != 0:
+        raise StmgError(st, "stmg_footprint failed")
+    return b.value
 
 
 def _ptr(t, dtype, numel, name):
@@ -229,6 +242,12 @@ class Solver:
 
     def set_timing(self, on=True):
         self._check(self.lib.stmg_set_timing(self.h, int(on)), "set_timing")
+
+    def set_physics(self, nu, tau, problem):
+        if isinstance(problem, str):
+            problem = PROBLEMS[problem]
+        self._check(self.lib.stmg_set_physics(self.h, float(nu), float(tau), int(problem)), "set_physics")
+        self.params.nu, self.params.tau, self.params.problem = nu, tau, problem
 
     KERNEL_CLASSES = ("apply_fp64", "apply_precond", "residual", "vanka_apply", "vanka_build", "mass")
 
