@@ -55,6 +55,7 @@ class Result:
     gmres_its: int
     checksum: float
     solution: object = None
+    error: object = None
 
 
 def poisson_stream(n_requests, rate, seed, shapes2d=(16, 32, 64, 128, 256), shapes3d=(8, 12, 16, 24, 32, 48),
@@ -179,12 +180,12 @@ class Server:
             start = now()
             try:
                 rc, nst, st, chk, sol = self.solve_fn(w, req, streams[w])
-            except Exception:
-                rc, nst, st, chk, sol = -1, 0, {}, float("nan"), None
+            except Exception as exc:                       # reported in the result, not raised
+                rc, nst, st, chk, sol = -1, 0, {"error": repr(exc)}, float("nan"), None
             end = now()
             with self.lock:
                 results[req.rid] = Result(req.rid, rc, nst, req.arrival, start, end, st.get("newton_its", 0),
-                                          st.get("gmres_its_total", 0), chk, sol)
+                                          st.get("gmres_its_total", 0), chk, sol, st.get("error"))
                 free.append(w)
                 self.lock.notify_all()
 

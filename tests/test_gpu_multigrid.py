@@ -106,11 +106,15 @@ def test_smoother_and_vcycle_match_oracle(d, n, r, k, amp, prec):
     assert _rel(_np(z), mg.vcycle(r0)) < tol_v
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("d,n,r,k,amp,nu,tau,pname", [
-    (2, 8, 1, 1, 0.0, 1e-2, 0.1, "TG2D"),       # 2D 8x8, Q2/P1, DG(1), dt = 0.1, Re = 100
-    (2, 8, 2, 2, 0.1, 1e-3, 0.05, "TG2D"),      # small case of the Q3/P2/DG(2) mapped workload
-    (2, 8, 1, 2, 0.1, 1e-2, 0.1, "MMS2D"),
+@pytest.mark.parametrize("precision,d,n,r,k,amp,nu,tau,pname", [
+    ("fp64", 2, 8, 1, 1, 0.0, 1e-2, 0.1, "TG2D"),   # 2D 8x8, Q2/P1, DG(1), dt = 0.1, Re = 100
+    ("fp32", 2, 8, 1, 1, 0.0, 1e-2, 0.1, "TG2D"),
+    ("fp64", 2, 8, 2, 2, 0.1, 1e-3, 0.05, "TG2D"),  # small case of the Q3/P2/DG(2) mapped workload
+    ("fp32", 2, 8, 2, 2, 0.1, 1e-3, 0.05, "TG2D"),
+    ("fp64", 2, 8, 1, 2, 0.1, 1e-2, 0.1, "MMS2D"),
+    ("fp32", 2, 8, 1, 2, 0.1, 1e-2, 0.1, "MMS2D"),
+    ("fp32", 3, 4, 1, 1, 0.1, 1.0 / 400, 0.05, "TG3D"),
+    ("fp32", 3, 4, 1, 0, 0.0, 1e-2, 0.05, "MMS3D"),
 ])
 def test_slab_solve_reaches_tolerance_and_matches_exact_solution(precision, d, n, r, k, amp, nu, tau, pname):
     import torch

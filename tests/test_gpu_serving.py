@@ -18,7 +18,7 @@ def test_mixed_stream_results_equal_solo_results():
     mix = Server(workers=3, keep_solutions=True)
     res = mix.run(reqs, realtime=False)
     mix.close()
-    assert all(r.status == 0 for r in res), [r.status for r in res]
+    assert all(r.status == 0 for r in res), [(r.status, r.error) for r in res]
     rep = report(res)
     assert rep["completed"] == len(reqs) and rep["p99_s"] >= rep["p50_s"]
     for q, r in zip(reqs, res):
