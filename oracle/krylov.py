@@ -179,7 +179,7 @@ DEFAULTS = dict(rtol=1e-8, atol=1e-12, maxit=20, ew_eta0=0.4, ew_c=0.5, ew_theta
 class SlabSolver:
     """Newton-FGMRES with hp-STMG on one configuration (all FP64)."""
 
-    def __init__(self, d, n, r, k, vertices, tau, prob, omega=0.3, max_h=-1, omega_p=1.0, nu1=1, nu2=1,
+    def __init__(self, d, n, r, k, vertices, tau, prob, omega=None, max_h=-1, omega_p=1.0, nu1=1, nu2=1,
                  **overrides):
         self.mg = Multigrid(d, n, r, k, vertices, tau, prob.nu, omega=omega, max_h=max_h, omega_p=omega_p,
                             nu1=nu1, nu2=nu2)

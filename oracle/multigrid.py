@@ -17,7 +17,7 @@ space-time Vanka smoother), restated as plain assembled linear algebra:
   finest degree factor), which makes the penalty term of the level operator equal to its
   Galerkin product P^T A P on nested meshes; with the level's own h and degree the coarse
   penalty is too weak and the V-cycle diverges;
-* Vanka (Eq. LVS, vanka0): additive over cells, patch = all velocity and pressure DoFs of the
+* Vanka (Eq. LVS, vanka0): additive over cells, damping omega = 1.2 / 2^d unless given, patch = all velocity and pressure DoFs of the
   cell at all time nodes, patch matrix = the global submatrix R_K J~ R_K^T of the midpoint
   surrogate J~ (Eq. DefTildeHn, DefVnAst), inverted by dense LU with partial pivoting;
 * V-cycle with nu1 / nu2 sweeps; coarsest level: dense LU of the assembled Jacobian bordered by
@@ -241,8 +241,12 @@ class CoarseSolver:
 class Multigrid:
     """hp-STMG V-cycle: z = B^{-1} r on the finest level (Sec. 4.2)."""
 
-    def __init__(self, d, n, r, k, vertices, tau, nu, omega=0.3, nu1=1, nu2=1, omega_p=1.0,
+    def __init__(self, d, n, r, k, vertices, tau, nu, omega=None, nu1=1, nu2=1, omega_p=1.0,
                  gamma=(10.0, 10.0), bconv=True, max_h=-1):
+        # Eq. vanka0 leaves omega open; the additive sum puts each velocity vertex in up to 2^d
+        # patches, so the default damping is 1.2 / 2^d (0.3 in 2D, 0.15 in 3D)
+        if omega is None:
+            omega = 1.2 / 2 ** d
         p0 = r + 1
         self.levels = [Level(d, ln, lr, lk, lv, tau, nu, gamma, bconv, hscale=(ln / n) / (p0 * (p0 + 1)))
                        for ln, lr, lk, lv in hierarchy(d, n, r, k, vertices, max_h)]

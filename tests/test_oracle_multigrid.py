@@ -1,0 +1,158 @@
+"""Pins of the oracle's hp-STMG pieces (Sec. 4.2-4.3) against facts that do not come from the
+oracle itself:
+
+* canonical-embedding prolongation: a polynomial that the coarse space holds is reproduced
+  exactly at the fine nodes (velocity: tensor polynomials of degree r_c + 1 on GLL nodes placed
+  from the closed-form Gauss-Lobatto points; pressure: coarse modal functions evaluated at random
+  points of the fine cells; time: polynomials of degree k_c at the Radau points);
+* state interpolation: a fine polynomial evaluated at the coarse nodes;
+* Galerkin identity: on nested Cartesian meshes at zero state, the rediscretised level operator
+  equals P^T J_fine P exactly (mass, viscous, pressure, Nitsche terms are all integrated exactly
+  and the coarse levels carry the finest Nitsche length) -- a transposed, mis-scaled or
+  mis-ordered transfer, or a wrong coarse penalty, breaks it;
+* coarse solve: for r in the range of J it returns x with J x = r and zero pressure mean;
+* the V-cycle as a stationary iteration contracts the residual (2D and 3D, default damping).
+"""
+import itertools
+
+import numpy as np
+import pytest
+from numpy.polynomial import legendre as npleg
+
+from oracle import forms, multigrid
+from oracle.reference import TimeData, gauss_lobatto_01, pressure_modes
+from paper_2602_13841_gb300 import inputs
+
+
+def _grid_positions(n, r):
+    """Global 1D GLL node positions of an n-cell Q_{r+1} line in [0, 1] (closed-form nodes)."""
+    g = gauss_lobatto_01(r + 2)
+    return np.array([(c + g[i]) / n for c in range(n) for i in range(r + 1)] + [1.0])
+
+
+def _tensor_values(d, x1, f):
+    """f at the tensor grid x1^d, x fastest (lexicographic node order of the slab layout)."""
+    pts = np.array(list(itertools.product(*([x1] * d))))[:, ::-1]
+    return f(pts)
+
+
+def _poly(d, deg, seed):
+    rng = np.random.default_rng(seed)
+    exps = [e for e in itertools.product(range(deg + 1), repeat=d)]
+    coef = rng.standard_normal(len(exps))
+
+    def f(p):
+        return sum(c * np.prod([p[:, l] ** e[l] for l in range(d)], axis=0) for c, e in zip(coef, exps))
+    return f
+
+
+@pytest.mark.parametrize("d,nf,rf,nc,rc", [(2, 4, 2, 4, 1), (2, 4, 1, 2, 1), (2, 6, 3, 6, 1), (3, 2, 2, 2, 1),
+                                           (3, 4, 1, 2, 1)])
+def test_velocity_prolongation_reproduces_coarse_polynomials(d, nf, rf, nc, rc):
+    f = _poly(d, rc + 1, 3)
+    vc = _tensor_values(d, _grid_positions(nc, rc), f)
+    vf = _tensor_values(d, _grid_positions(nf, rf), f)
+    P = multigrid.velocity_prolongation(d, nf, rf, nc, rc)
+    assert np.abs(P @ vc - vf).max() < 1e-12 * np.abs(vf).max()
+
+
+@pytest.mark.parametrize("d,nf,rf,nc,rc", [(2, 4, 2, 4, 1), (2, 4, 1, 2, 1), (3, 2, 2, 2, 1), (3, 4, 1, 2, 1)])
+def test_velocity_state_interpolation_evaluates_fine_polynomials(d, nf, rf, nc, rc):
+    f = _poly(d, rf + 1, 4)
+    vf = _tensor_values(d, _grid_positions(nf, rf), f)
+    vc = _tensor_values(d, _grid_positions(nc, rc), f)
+    I = multigrid.velocity_interpolation(d, nf, rf, nc, rc)
+    assert np.abs(I @ vf - vc).max() < 1e-12 * np.abs(vc).max()
+
+
+def _eval_pressure(d, n, r, coef, pts):
+    """Modal P_r^disc function (cell-major, x-fastest cells) at global points of [0,1]^d."""
+    modes = pressure_modes(r, d)
+    out = np.zeros(len(pts))
+    for q, x in enumerate(pts):
+        cell = np.minimum((x * n).astype(int), n - 1)
+        xi = x * n - cell
+        c = int(np.dot(cell, n ** np.arange(d)))
+        for m, deg in enumerate(modes):
+            val = 1.0
+            for l in range(d):
+                e = np.zeros(deg[l] + 1)
+                e[deg[l]] = 1.0
+                val *= npleg.legval(2.0 * xi[l] - 1.0, e)
+            out[q] += coef[c * len(modes) + m] * val
+    return out
+
+
+@pytest.mark.parametrize("d,nf,rf,nc,rc", [(2, 4, 2, 4, 1), (2, 4, 1, 2, 1), (2, 4, 3, 2, 1), (3, 2, 2, 2, 1),
+                                           (3, 4, 1, 2, 1)])
+def test_pressure_prolongation_is_exact_reexpansion(d, nf, rf, nc, rc):
+    mf, mc = pressure_modes(rf, d), pressure_modes(rc, d)
+    rng = np.random.default_rng(11)
+    coef_c = rng.standard_normal(nc ** d * len(mc))
+    P = multigrid.pressure_prolongation(d, nf, rf, nc, rc, mf, mc)
+    coef_f = P @ coef_c
+    pts = rng.uniform(0.0, 1.0, size=(60, d))
+    want = _eval_pressure(d, nc, rc, coef_c, pts)
+    got = _eval_pressure(d, nf, rf, coef_f, pts)
+    assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("kf,kc", [(2, 1), (1, 0), (2, 0), (1, 1)])
+def test_time_prolongation_reproduces_coarse_polynomials(kf, kc):
+    tf, tc = TimeData(kf, 1.0), TimeData(kc, 1.0)
+    c = np.random.default_rng(kf * 10 + kc).standard_normal(kc + 1)
+    g = lambda t: np.polyval(c, t)
+    E = multigrid.time_prolongation(kf, kc)
+    assert np.abs(E @ g(tc.that) - g(tf.that)).max() < 1e-13
+
+
+@pytest.mark.parametrize("d,n,r,k", [(2, 4, 1, 1), (2, 4, 2, 2), (2, 4, 3, 1), (3, 2, 2, 0), (3, 4, 1, 1)])
+def test_galerkin_identity_on_nested_cartesian_meshes(d, n, r, k):
+    verts = inputs.vertices(d, n, 0.0, 1)
+    mg = multigrid.Multigrid(d, n, r, k, verts, 0.05, 1e-2)
+    mg.setup(np.zeros(mg.levels[0].Nst))
+    assert len(mg.levels) >= 2
+    for l in range(len(mg.levels) - 1):
+        G = (mg.P[l].T @ mg.J[l] @ mg.P[l]).toarray()
+        C = mg.J[l + 1].toarray()
+        assert np.abs(G - C).max() < 1e-12 * np.abs(C).max(), l
+
+
+@pytest.mark.parametrize("d,n,r,k,amp", [(2, 2, 1, 1, 0.1), (2, 4, 2, 0, 0.0), (3, 2, 1, 1, 0.1)])
+def test_coarse_solve_inverts_on_the_range(d, n, r, k, amp):
+    verts = inputs.vertices(d, n, amp, 2)
+    mg = multigrid.Multigrid(d, n, r, k, verts, 0.05, 1e-2, max_h=0)
+    L = mg.levels[-1]
+    mg.setup(inputs.uniform(mg.levels[0].Nst, 3))
+    J = mg.J[-1]
+    y = inputs.uniform(L.Nst, 4)
+    rhs = J @ y
+    x = mg.coarse.solve(rhs)
+    assert np.abs(J @ x - rhs).max() < 1e-10 * np.abs(rhs).max()
+    w = np.einsum("kq,qm->km", L.space.JxW, L.space.ref.psi).ravel()
+    for a in range(k + 1):
+        P = x[L.lay.poff(a):L.lay.poff(a) + L.lay.Np]
+        assert abs(np.dot(w, P)) < 1e-10 * np.abs(P).max()
+
+
+@pytest.mark.parametrize("d,n,r,k,nu,rate", [(2, 8, 1, 1, 1e-2, 0.45), (2, 8, 2, 2, 1e-3, 0.6),
+                                              (3, 4, 1, 1, 1e-2, 0.7)])
+def test_vcycle_iteration_contracts(d, n, r, k, nu, rate):
+    """x <- x + B^{-1}(b - J x) at a smooth state (the interpolated Taylor-Green field at every
+    time node): the residual falls at least by `rate` per cycle on average over 6 cycles."""
+    from oracle import problems
+    verts = inputs.vertices(d, n, 0.1, 9)
+    mg = multigrid.Multigrid(d, n, r, k, verts, 0.05, nu)
+    L = mg.levels[0]
+    prob = problems.make("TG2D" if d == 2 else "TG3D", nu)
+    V = forms.interpolate_velocity(L.space, prob.v0)
+    U = np.concatenate([np.tile(V, k + 1), np.zeros((k + 1) * L.lay.Np)])
+    mg.setup(U)
+    J = mg.J[0]
+    b = J @ inputs.uniform(L.Nst, 6)
+    x = np.zeros(L.Nst)
+    r0 = np.linalg.norm(b)
+    for _ in range(6):
+        x = x + mg.vcycle(b - J @ x)
+    red = (np.linalg.norm(b - J @ x) / r0) ** (1.0 / 6.0)
+    assert red < rate, red
