@@ -67,7 +67,8 @@ typedef struct {
   int n_levels_h;      /* number of h-coarsenings; -1: coarsen while n even and n/2 >= 2 */
   int precond_precision; /* stmg_precision of the multigrid preconditioner */
   int nu1, nu2;        /* Vanka pre/post sweeps (Sec. 5.1: 1, 1) */
-  double omega;        /* Vanka damping (Eq. vanka0) */
+  double omega;        /* Vanka damping of the velocity DoFs (Eq. vanka0); <= 0 (default):
+                          1.2 / 2^d, i.e. 0.3 in 2D, 0.15 in 3D (a vertex lies in 2^d patches) */
   double newton_rtol, newton_atol; int newton_maxit;            /* Sec. 5: 1e-8, 1e-12 */
   double ew_eta0, ew_c, ew_theta, ew_min, ew_max;               /* Alg. 1: 0.4, 0.5, 1.5, 1e-3, 0.8 */
   double ls_lambda0, ls_c, ls_tau, ls_alpha_min; int ls_maxbt, ls_window; /* Alg. 2 */
@@ -75,6 +76,9 @@ typedef struct {
   double rebuild_thetaN, rebuild_thetaL; int rebuild_kappa_abs; /* Alg. 1 rebuild triggers */
   int stag_s; double stag_theta;                                /* FGMRES stagnation window */
   double omega_p;      /* Vanka relaxation of the pressure DoFs (velocity DoFs use omega) */
+  int vanka_fp16;      /* 1: store the Vanka patch inverses as FP16 with one FP32 scale per patch
+                          (half the smoother's memory traffic; the apply still accumulates in
+                          the preconditioner precision).  0 (default): preconditioner precision. */
 } stmg_params;
 
 /* Fill *p with the paper's defaults (Sec. 5, Alg. 1-2) for a d-dimensional problem. */

@@ -16,6 +16,7 @@ cudaError_t MG<T>::allocate(Handle* hh) {
   h = hh;
   nl = (int)h->levels.size();
   U.resize(nl); r.resize(nl); z.resize(nl); t.resize(nl); q.resize(nl); inv.assign(nl, nullptr);
+  invh.assign(nl, nullptr); iscale.assign(nl, nullptr);
   size_t ea = 0, eb = 0, em = 0, nv = 0;
   try {
     for (int l = 0; l < nl; ++l) {
@@ -28,7 +29,12 @@ cudaError_t MG<T>::allocate(Handle* hh) {
       if (l < nl - 1) {
         if (!vanka_supported(lv, sizeof(T))) { smoothable = false; continue; }
         size_t m = vanka_patch_size(lv);
-        inv[l] = (T*)h->dalloc((size_t)(lv.Np / lv.npc) * m * m * sizeof(T));
+        if (h->prm.vanka_fp16) {
+          invh[l] = h->dalloc((size_t)(lv.Np / lv.npc) * m * m * 2);
+          iscale[l] = (float*)h->dalloc((size_t)(lv.Np / lv.npc) * sizeof(float));
+        } else {
+          inv[l] = (T*)h->dalloc((size_t)(lv.Np / lv.npc) * m * m * sizeof(T));
+        }
         size_t nc = lv.Np / lv.npc;
         ea = std::max(ea, nc * vanka_elem_size(lv, 0));
         eb = std::max(eb, nc * vanka_elem_size(lv, 1));
@@ -84,7 +90,7 @@ cudaError_t MG<T>::setup(const double* U64) {
   }
   for (int l = 0; l + 1 < nl; ++l) {
     h->kbegin(KC_VANKA_BUILD);
-    CKE(vanka_build<T>(h->levels[l], h->pb, U[l], vstar, EA, EB, EM, inv[l], status, s));
+    CKE(vanka_build<T>(h->levels[l], h->pb, U[l], vstar, EA, EB, EM, inv[l], invh[l], iscale[l], status, s));
     h->kend(KC_VANKA_BUILD, 0.0, 4);
   }
   // coarse: assemble J_c at the coarse state by a batched apply to the identity
@@ -142,8 +148,9 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
     for (int c = 0; c < lv.ncolors; ++c) {
       // algorithmic bytes: the patch inverses of the colour's cells, residual gather, d update
       h->kbegin(KC_VANKA_APPLY);
-      CKE(vanka_apply<T>(lv, h->pb, inv[l], res, d, omega, h->prm.omega_p, c, s));
-      h->kend(KC_VANKA_APPLY, (double)lv.colors[c].count * (m * m + 3.0 * m) * sizeof(T));
+      CKE(vanka_apply<T>(lv, h->pb, inv[l], invh[l], iscale[l], res, d, omega, h->prm.omega_p, c, s));
+      const double ib = invh[l] ? m * m * 2.0 + 4.0 : m * m * sizeof(T);
+      h->kend(KC_VANKA_APPLY, (double)lv.colors[c].count * (ib + 3.0 * m * sizeof(T)));
     }
   }
   return cudaSuccess;

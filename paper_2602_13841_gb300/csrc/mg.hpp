@@ -21,7 +21,9 @@ struct MG {
   Handle* h = nullptr;
   int nl = 0;
   std::vector<T*> U, r, z, t, q;     // per level: state, rhs, correction, temporaries
-  std::vector<T*> inv;               // per smoothed level: patch inverses
+  std::vector<T*> inv;               // per smoothed level: patch inverses (precision T) ...
+  std::vector<void*> invh;           // ... or FP16 patch inverses (params.vanka_fp16) ...
+  std::vector<float*> iscale;        // ... with one FP32 scale per patch
   std::vector<Transfer> tr;
   T *EA = nullptr, *EB = nullptr, *EM = nullptr, *vstar = nullptr;
   int* status = nullptr;             // device flag: zero pivot in a patch
@@ -61,10 +63,11 @@ struct MG {
 // Launch helpers implemented in vanka.cu (templated on T).
 template <typename T>
 cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar, T* EA, T* EB, T* EM,
-                        T* inv, int* status, cudaStream_t s);
+                        T* inv, void* invh, float* scale, int* status, cudaStream_t s);
+// inv: patch inverses of precision T, or (invh non-null) FP16 inverses scaled by scale[cell].
 template <typename T>
-cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const T* res, T* d, double omega,
-                        double omega_p, int color, cudaStream_t s);
+cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
+                        const T* res, T* d, double omega, double omega_p, int color, cudaStream_t s);
 size_t vanka_patch_size(const Level& lv);            // m_st
 size_t vanka_elem_size(const Level& lv, int which);  // entries per cell of EA (0), EB (1), EM (2)
 bool vanka_supported(const Level& lv, size_t esize);

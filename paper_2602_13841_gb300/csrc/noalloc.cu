@@ -56,7 +56,8 @@ static cudaError_t sweep_noalloc(Handle* h, MG<T>& mg, int l, const T* rhs, T* d
       res = q;
     }
     for (int c = 0; c < lv.ncolors; ++c) {
-      cudaError_t e = vanka_apply<T>(lv, h->pb, mg.inv[l], res, d, h->prm.omega, h->prm.omega_p, c, s);
+      cudaError_t e = vanka_apply<T>(lv, h->pb, mg.inv[l], mg.invh[l], mg.iscale[l], res, d, h->prm.omega,
+                                     h->prm.omega_p, c, s);
       if (e != cudaSuccess) return e;
     }
   }

@@ -118,7 +118,7 @@ void stmg_params_default(stmg_params* p) {
   p->nu = 1e-2; p->tau = 0.1; p->gamma1 = 10.0; p->gamma2 = 10.0;
   p->problem = STMG_TG2D; p->bconv = 1; p->n_levels_h = -1;
   p->precond_precision = STMG_FP32;
-  p->nu1 = 1; p->nu2 = 1; p->omega = 0.3;
+  p->nu1 = 1; p->nu2 = 1; p->omega = 0.0;
   p->newton_rtol = 1e-8; p->newton_atol = 1e-12; p->newton_maxit = 20;
   p->ew_eta0 = 0.4; p->ew_c = 0.5; p->ew_theta = 1.5; p->ew_min = 1e-3; p->ew_max = 0.8;
   p->ls_lambda0 = 1.0; p->ls_c = 1e-4; p->ls_tau = 0.5; p->ls_alpha_min = 1e-3;
@@ -127,6 +127,7 @@ void stmg_params_default(stmg_params* p) {
   p->rebuild_thetaN = 1.0; p->rebuild_thetaL = 2.0; p->rebuild_kappa_abs = 50;
   p->stag_s = 3; p->stag_theta = 0.95;
   p->omega_p = 1.0;
+  p->vanka_fp16 = 0;
 }
 
 stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
@@ -158,7 +159,7 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
     tot += 5.0 * nst[l] * es;                                            // level vectors
     if (l + 1 < lv.size()) {
       double nl = std::pow(lr + 2.0, d), mv = d * nl, m = (lk + 1.0) * (mv + npc);
-      tot += cells * m * m * es;                                         // patch inverses
+      tot += p->vanka_fp16 ? cells * (m * m * 2.0 + 4.0) : cells * m * m * es;  // patch inverses
       ea = std::max(ea, cells * mv * mv); eb = std::max(eb, cells * npc * mv); em = std::max(em, cells * nl * nl);
       nvmax = std::max(nvmax, Nv);
       tot += 3.0 * std::max((lk + 1.0) * Nv, (lk + 1.0) * Np) * es;      // transfer scratch
@@ -192,6 +193,8 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
     return STMG_ERR_ARG;
   auto h = std::make_unique<Handle>();
   h->prm = *p;
+  // omega <= 0: 1.2 / 2^d -- each velocity vertex lies in up to 2^d of the additive patches
+  if (!(h->prm.omega > 0)) h->prm.omega = 1.2 / (double)(1 << p->dim);
   h->stream = (cudaStream_t)stream;
   h->pb = Problem{p->nu, p->tau, p->gamma1, p->gamma2, p->bconv, p->problem};
   const int d = p->dim, n = p->n_cells_1d;

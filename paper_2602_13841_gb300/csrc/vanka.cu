@@ -62,12 +62,12 @@ __global__ void k_midpoint(const T* __restrict__ U, T* __restrict__ vs, int64_t 
 
 template <typename T, int D, int N>
 static cudaError_t build_dn(const Level& lv, const Problem& pb, const T* U, T* vstar, T* EA, T* EB, T* EM,
-                            T* inv, int* status, cudaStream_t s) {
+                            T* inv, void* invh, float* scale, int* status, cudaStream_t s) {
   Tab<T> tb = make_tab<T>(lv.tabs, pb.tau);
   int64_t ncells = lv.Np / lv.npc;
   int64_t g = (lv.Nv + 255) / 256; if (g > 152 * 8) g = 152 * 8;
   k_midpoint<T><<<(int)g, 256, 0, s>>>(U, vstar, lv.Nv, lv.k + 1, tb);
-  VankaArgs<T> V{level_args<T>(lv, pb, 0.0), vstar, EA, EB, EM, inv, status};
+  VankaArgs<T> V{level_args<T>(lv, pb, 0.0), vstar, EA, EB, EM, inv, (__half*)invh, scale, status};
   size_t es = elem_smem<D, N>(sizeof(T));
   cudaError_t e = cudaFuncSetAttribute(k_elem<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)es);
   if (e != cudaSuccess) return e;
@@ -82,10 +82,10 @@ static cudaError_t build_dn(const Level& lv, const Problem& pb, const T* U, T* v
 
 template <typename T>
 cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar, T* EA, T* EB, T* EM,
-                        T* inv, int* status, cudaStream_t s) {
+                        T* inv, void* invh, float* scale, int* status, cudaStream_t s) {
   if (!vanka_supported(lv, sizeof(T))) return cudaErrorNotSupported;
   const int N = lv.r + 2;
-#define STMG_B(DD, NN) return build_dn<T, DD, NN>(lv, pb, U, vstar, EA, EB, EM, inv, status, s)
+#define STMG_B(DD, NN) return build_dn<T, DD, NN>(lv, pb, U, vstar, EA, EB, EM, inv, invh, scale, status, s)
   if (lv.d == 2) { if (N == 3) STMG_B(2, 3); if (N == 4) STMG_B(2, 4); if (N == 5) STMG_B(2, 5); }
   else { if (N == 3) STMG_B(3, 3); if (N == 4) STMG_B(3, 4); }
 #undef STMG_B
@@ -93,25 +93,30 @@ cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar
 }
 
 template <typename T, int D, int N>
-static cudaError_t apply_dn(const Level& lv, const Problem& pb, const T* inv, const T* res, T* d, double omega,
-                            double omega_p, int color, cudaStream_t s) {
+static cudaError_t apply_dn(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
+                            const T* res, T* d, double omega, double omega_p, int color, cudaStream_t s) {
   const ColorInfo& ci = lv.colors[color];
   if (ci.count == 0) return cudaSuccess;
   const int m = (int)vanka_patch_size(lv);
   int threads = ((m + 31) / 32) * 32;
   if (threads > 256) threads = 256;
   size_t smem = sizeof(T) * (((m + 1) & ~1)) + sizeof(int64_t) * m + 16;
-  k_vanka_apply<T, D, N><<<ci.count, threads, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, res, d, (T)omega,
-                                                         (T)omega_p, lv.k + 1, lv.npc, ci);
+  if (invh)
+    k_vanka_apply<T, __half, D, N><<<ci.count, threads, smem, s>>>(level_args<T>(lv, pb, 0.0), (const __half*)invh,
+                                                                   scale, res, d, (T)omega, (T)omega_p, lv.k + 1,
+                                                                   lv.npc, ci);
+  else
+    k_vanka_apply<T, T, D, N><<<ci.count, threads, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, nullptr, res, d,
+                                                              (T)omega, (T)omega_p, lv.k + 1, lv.npc, ci);
   note_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const T* res, T* d, double omega,
-                        double omega_p, int color, cudaStream_t s) {
+cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
+                        const T* res, T* d, double omega, double omega_p, int color, cudaStream_t s) {
   const int N = lv.r + 2;
-#define STMG_A(DD, NN) return apply_dn<T, DD, NN>(lv, pb, inv, res, d, omega, omega_p, color, s)
+#define STMG_A(DD, NN) return apply_dn<T, DD, NN>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, s)
   if (lv.d == 2) { if (N == 3) STMG_A(2, 3); if (N == 4) STMG_A(2, 4); if (N == 5) STMG_A(2, 5); }
   else { if (N == 3) STMG_A(3, 3); if (N == 4) STMG_A(3, 4); }
 #undef STMG_A
@@ -119,12 +124,12 @@ cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const 
 }
 
 template cudaError_t vanka_build<float>(const Level&, const Problem&, const float*, float*, float*, float*, float*,
-                                        float*, int*, cudaStream_t);
+                                        float*, void*, float*, int*, cudaStream_t);
 template cudaError_t vanka_build<double>(const Level&, const Problem&, const double*, double*, double*, double*,
-                                         double*, double*, int*, cudaStream_t);
-template cudaError_t vanka_apply<float>(const Level&, const Problem&, const float*, const float*, float*, double,
-                                        double, int, cudaStream_t);
-template cudaError_t vanka_apply<double>(const Level&, const Problem&, const double*, const double*, double*,
-                                         double, double, int, cudaStream_t);
+                                         double*, double*, void*, float*, int*, cudaStream_t);
+template cudaError_t vanka_apply<float>(const Level&, const Problem&, const float*, const void*, const float*,
+                                        const float*, float*, double, double, int, cudaStream_t);
+template cudaError_t vanka_apply<double>(const Level&, const Problem&, const double*, const void*, const float*,
+                                         const double*, double*, double, double, int, cudaStream_t);
 
 }  // namespace stmg

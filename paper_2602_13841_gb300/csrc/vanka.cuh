@@ -16,6 +16,8 @@
 // Sweep (additive, damped): d <- d + omega sum_K R_K^T S~_K^{-1} R_K (rhs - J d); cells are
 // updated in 2^d colours so that the scatter is race free and deterministic.
 #pragma once
+#include <cuda_fp16.h>
+
 #include "operator.cuh"
 
 namespace stmg {
@@ -27,9 +29,30 @@ struct VankaArgs {
   T* EA;                // [cells][mv][mv]
   T* EB;                // [cells][npc][mv]
   T* EM;                // [cells][nl][nl]
-  T* inv;               // [cells][mst][mst] column-major inverse
+  T* inv;               // [cells][mst][mst] column-major inverse (storage in T), or
+  __half* invh;         // the same scaled to [-1, 1] in FP16 with one FP32 factor per cell
+  float* scale;         // [cells]
   int* status;          // set to 1 on a zero pivot
 };
+
+// max |x| over the block (all threads receive it)
+template <typename T>
+__device__ inline T block_absmax(T v) {
+  __shared__ T wmax[32];
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) wmax[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (lane < (int)((blockDim.x + 31) >> 5)) ? wmax[lane] : (T)0;
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if (lane == 0) wmax[0] = v;
+  }
+  __syncthreads();
+  v = wmax[0];
+  __syncthreads();
+  return v;
+}
 
 template <int D>
 __device__ inline void cell_coords(int64_t cell, int n, int* cc) {
@@ -388,6 +411,21 @@ __global__ void k_patch(VankaArgs<T> V, Tab<T> tb, int64_t ncells) {
   __syncthreads();
   bool ok = gauss_jordan<T>(S, m, m, piv, colbuf);
   if (!ok) { if (tid == 0) *V.status = 1; return; }
+  if (V.invh) {
+    T mx = 0;
+    for (int ent = tid; ent < m * m; ent += nt) mx = fmax(mx, fabs(S[ent]));
+    mx = block_absmax<T>(mx);
+    // the scale is held in FP32: divide by exactly the value the apply multiplies by
+    const float sc = mx > 0 ? (float)mx : 1.f;
+    const T isc = (T)1 / (T)sc;
+    if (tid == 0) V.scale[cell] = sc;
+    __half* inv = V.invh + cell * (int64_t)m * m;
+    for (int ent = tid; ent < m * m; ent += nt) {
+      const int j = ent / m, i = ent % m;
+      inv[ent] = __float2half_rn((float)(S[i * m + j] * isc));
+    }
+    return;
+  }
   T* inv = V.inv + cell * (int64_t)m * m;
   for (int ent = tid; ent < m * m; ent += nt) {
     const int j = ent / m, i = ent % m;          // column-major store: inv[j][i] = S^{-1}[i][j]
@@ -397,9 +435,15 @@ __global__ void k_patch(VankaArgs<T> V, Tab<T> tb, int64_t ncells) {
 
 // ---------------------------------------------------------------------------- sweep
 // d[patch] += omega * S~^{-1} res[patch] for the cells of one colour (one block per cell).
-template <typename T, int D, int N>
-__global__ void k_vanka_apply(LevelArgs<T> L, const T* __restrict__ inv, const T* __restrict__ res,
-                              T* __restrict__ d, T omega, T omega_p, int kp1, int npc, ColorInfo ci) {
+// The inverse is stored in SI (T, or FP16 scaled per cell by scale[cell]); accumulation in T.
+__device__ __forceinline__ float ld_inv(const __half* p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ float ld_inv(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double ld_inv(const double* p) { return __ldg(p); }
+
+template <typename T, typename SI, int D, int N>
+__global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const float* __restrict__ scale,
+                              const T* __restrict__ res, T* __restrict__ d, T omega, T omega_p, int kp1, int npc,
+                              ColorInfo ci) {
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int m = kp1 * (MV + npc);
@@ -426,20 +470,21 @@ __global__ void k_vanka_apply(LevelArgs<T> L, const T* __restrict__ inv, const T
     r[l] = res[g];
   }
   __syncthreads();
-  const T* Sinv = inv + cell * (int64_t)m * m;
+  const SI* Sinv = inv + cell * (int64_t)m * m;
+  const T sc = scale ? (T)scale[cell] : (T)1;
   for (int i = tid; i < m; i += nt) {
     // four independent accumulators keep several column loads in flight per thread
     T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    const T* col = Sinv + i;
+    const SI* col = Sinv + i;
     int j = 0;
     for (; j + 3 < m; j += 4) {
-      a0 += __ldg(col + (int64_t)j * m) * r[j];
-      a1 += __ldg(col + (int64_t)(j + 1) * m) * r[j + 1];
-      a2 += __ldg(col + (int64_t)(j + 2) * m) * r[j + 2];
-      a3 += __ldg(col + (int64_t)(j + 3) * m) * r[j + 3];
+      a0 += (T)ld_inv(col + (int64_t)j * m) * r[j];
+      a1 += (T)ld_inv(col + (int64_t)(j + 1) * m) * r[j + 1];
+      a2 += (T)ld_inv(col + (int64_t)(j + 2) * m) * r[j + 2];
+      a3 += (T)ld_inv(col + (int64_t)(j + 3) * m) * r[j + 3];
     }
-    for (; j < m; ++j) a0 += __ldg(col + (int64_t)j * m) * r[j];
-    d[gidx[i]] += (i < kp1 * MV ? omega : omega_p) * ((a0 + a1) + (a2 + a3));
+    for (; j < m; ++j) a0 += (T)ld_inv(col + (int64_t)j * m) * r[j];
+    d[gidx[i]] += (i < kp1 * MV ? omega : omega_p) * sc * ((a0 + a1) + (a2 + a3));
   }
 }
 

@@ -29,13 +29,13 @@ def _np(t):
     return t.double().cpu().numpy()
 
 
-def _setup(d, n, r, k, amp, precision="fp64", omega=0.3, nu=0.01, tau=0.05, problem="TG2D", seed=5, **kw):
+def _setup(d, n, r, k, amp, precision="fp64", omega=None, nu=0.01, tau=0.05, problem="TG2D", seed=5, **kw):
     from paper_2602_13841_gb300 import stmg
     build_and_load()
     verts = inputs.vertices(d, n, amp, seed)
     prec = stmg.STMG_FP64 if precision == "fp64" else stmg.STMG_FP32
     p = stmg.default_params(dim=d, n_cells_1d=n, r=r, k=k, nu=nu, tau=tau, problem=problem,
-                            omega=omega, precond_precision=prec, **kw)
+                            omega=omega or 0.0, precond_precision=prec, **kw)
     S = stmg.Solver(p, verts)
     mg = multigrid.Multigrid(d, n, r, k, verts, tau, nu, omega=omega)
     return S, mg, verts
@@ -137,4 +137,67 @@ def test_slab_solve_reaches_tolerance_and_matches_exact_solution(precision, d, n
     got = _np(U)
     assert _rel(got[:nv], Ud[:nv]) < 1e-7
     # pressure: same up to the mean, which both remove
+    assert np.abs(got[nv:] - Ud[nv:]).max() < 1e-6 * max(np.abs(Ud[nv:]).max(), 1.0)
+
+
+@pytest.mark.parametrize("d,n,r,k,amp,prec", [(2, 8, 2, 2, 0.15, "fp64"), (2, 6, 1, 0, 0.1, "fp64"),
+                                              (2, 8, 2, 2, 0.15, "fp32"), (3, 4, 1, 1, 0.1, "fp32")])
+def test_fp16_patch_inverses(d, n, r, k, amp, prec):
+    """Vanka sweeps with the patch inverses stored as FP16 and one FP32 scale s = max|S^-1| per
+    patch.  FP64 preconditioner: equal, to 1e-6 relative, to the oracle sweep whose inverses are
+    rounded the same way (round(S^-1 / s) * s, round = nearest FP16); an entry whose rounding
+    falls on the other side of a tie between the two inverses moves by one FP16 unit.  FP32
+    preconditioner: within 2e-2 relative of the unrounded oracle sweep."""
+    import scipy.linalg as sla
+    import torch
+    S, mg, _ = _setup(d, n, r, k, amp, precision=prec, vanka_fp16=1)
+    dt = S.pdtype
+    L0 = mg.levels[0]
+    U = inputs.uniform(L0.Nst, 7)
+    mg.setup(U)
+    S.smoother_build(_t(U))
+    for l in range(len(mg.levels) - 1):
+        L = mg.levels[l]
+        sm = mg.smoothers[l]
+        rhs = inputs.uniform(L.Nst, 30 + l)
+        d0 = inputs.uniform(L.Nst, 40 + l)
+        res = rhs - mg.J[l] @ d0
+        upd = np.zeros(L.Nst)
+        for idx, lu in sm.patches:
+            Si = sla.lu_solve(lu, np.eye(len(idx)))
+            s = np.float32(np.abs(Si).max())
+            Q = (Si / np.float64(s)).astype(np.float32).astype(np.float16).astype(np.float64) * np.float64(s)
+            upd[idx] += Q @ res[idx]
+        want_q = d0 + sm.weights * upd
+        want = sm.sweep(mg.J[l], rhs, d0)
+        got = _t(d0, dt)
+        S.smoother_sweep(l, _t(rhs, dt), got, 1, zero_start=False)
+        if prec == "fp64":
+            assert _rel(_np(got), want_q) < 1e-6, l
+        else:
+            assert _rel(_np(got), want) < 2e-2, l
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_slab_solve_with_fp16_patch_inverses(precision):
+    """The FP16-stored smoother only changes the preconditioner: FGMRES still reaches the Newton
+    tolerance and the solution equals the exact discrete solution (2D 8x8, Q3/P2, DG(2))."""
+    import torch
+    d, n, r, k, amp, nu, tau, pname = 2, 8, 2, 2, 0.1, 1e-3, 0.05, "TG2D"
+    S, mg, verts = _setup(d, n, r, k, amp, precision=precision, nu=nu, tau=tau, problem=pname,
+                          newton_rtol=1e-10, newton_atol=0.0, vanka_fp16=1)
+    L0 = mg.levels[0]
+    prob = problems.make(pname, nu)
+    V0 = torch.empty(L0.lay.Nv, dtype=torch.float64, device="cuda")
+    S.initial_condition(V0)
+    U = torch.empty(L0.Nst, dtype=torch.float64, device="cuda")
+    S.initial_guess(V0, U)
+    rc, st = S.slab_solve(0.2, V0, U)
+    assert rc == 0 and st["res_final"] <= 1e-10 * st["res0"]
+    Vp = _np(V0)
+    U0 = np.concatenate([np.tile(Vp, k + 1), np.zeros((k + 1) * L0.lay.Np)])
+    Ud, _ = marching.newton_direct(L0.space, L0.td, U0, Vp, prob, 0.2, tol=1e-13)
+    nv = (k + 1) * L0.lay.Nv
+    got = _np(U)
+    assert _rel(got[:nv], Ud[:nv]) < 1e-7
     assert np.abs(got[nv:] - Ud[nv:]).max() < 1e-6 * max(np.abs(Ud[nv:]).max(), 1.0)
