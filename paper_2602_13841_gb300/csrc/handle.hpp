@@ -1,6 +1,7 @@
 // The opaque handle behind stmg_handle: parameters, stream, levels, multigrid, Krylov and
 // Newton work space, phase timers.
 #pragma once
+#include <stdexcept>
 #include <cuda_runtime.h>
 
 #include <memory>
@@ -30,6 +31,11 @@ struct PhaseTimer {
   void collect();            // after a stream synchronisation: add the spans to ms
   ~PhaseTimer();
   cudaEvent_t open_ = nullptr;
+};
+
+struct CudaFailure : std::runtime_error {
+  cudaError_t err;
+  explicit CudaFailure(cudaError_t e) : std::runtime_error(cudaGetErrorString(e)), err(e) {}
 };
 
 struct Handle {
@@ -72,6 +78,10 @@ struct Handle {
   }
   ~Handle();
   void* dalloc(size_t bytes);          // cudaMalloc tracked for release; throws std::bad_alloc
+  // host -> device copy of set-up data on the handle's stream, complete on return (the host
+  // buffer may be freed right after); throws CudaFailure.  No device-wide or legacy-stream
+  // synchronisation: other handles may be capturing graphs on their streams meanwhile.
+  void upload(void* dst, const void* src, size_t bytes);
   stmg_status fail(stmg_status s, const std::string& msg);
   cudaError_t ensure_mg();
   cudaError_t ensure_solver();

@@ -30,10 +30,10 @@ cudaError_t MG<T>::allocate(Handle* hh) {
         if (!vanka_supported(lv, sizeof(T))) { smoothable = false; continue; }
         size_t m = vanka_patch_size(lv);
         if (h->prm.vanka_fp16) {
-          invh[l] = h->dalloc((size_t)(lv.Np / lv.npc) * m * m * 2);
+          invh[l] = h->dalloc((size_t)(lv.Np / lv.npc) * vanka_inv_entries(lv) * 2);
           iscale[l] = (float*)h->dalloc((size_t)(lv.Np / lv.npc) * sizeof(float));
         } else {
-          inv[l] = (T*)h->dalloc((size_t)(lv.Np / lv.npc) * m * m * sizeof(T));
+          inv[l] = (T*)h->dalloc((size_t)(lv.Np / lv.npc) * vanka_inv_entries(lv) * sizeof(T));
         }
         size_t nc = lv.Np / lv.npc;
         ea = std::max(ea, nc * vanka_elem_size(lv, 0));
@@ -66,6 +66,8 @@ cudaError_t MG<T>::allocate(Handle* hh) {
     gj_piv = (int*)h->dalloc((size_t)Nb * sizeof(int));
   } catch (const std::bad_alloc&) {
     return cudaErrorMemoryAllocation;
+  } catch (const CudaFailure& f) {
+    return f.err;
   }
   return cudaSuccess;
 }
@@ -144,14 +146,17 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
       CKE(vaxpby<T>(lv.Nst, (T)1, rhs, (T)-1, q[l], s));
       res = q[l];
     }
+    // one timer span over the colour launches of the sweep (they run back to back);
+    // algorithmic bytes: the patch inverses of every cell, residual gather, d read and write
     const double m = (double)vanka_patch_size(lv);
+    const double ib = invh[l] ? m * m * 2.0 + 4.0 : m * m * sizeof(T);
+    int64_t cells = 0;
+    h->kbegin(KC_VANKA_APPLY);
     for (int c = 0; c < lv.ncolors; ++c) {
-      // algorithmic bytes: the patch inverses of the colour's cells, residual gather, d update
-      h->kbegin(KC_VANKA_APPLY);
       CKE(vanka_apply<T>(lv, h->pb, inv[l], invh[l], iscale[l], res, d, omega, h->prm.omega_p, c, s));
-      const double ib = invh[l] ? m * m * 2.0 + 4.0 : m * m * sizeof(T);
-      h->kend(KC_VANKA_APPLY, (double)lv.colors[c].count * (ib + 3.0 * m * sizeof(T)));
+      cells += lv.colors[c].count;
     }
+    h->kend(KC_VANKA_APPLY, (double)cells * (ib + 3.0 * m * sizeof(T)), lv.ncolors);
   }
   return cudaSuccess;
 }
@@ -203,17 +208,23 @@ cudaError_t MG<T>::vcycle_graph() {
     if (h->timing) h->capsink = &gspans;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) { h->capsink = nullptr; return e; }
+    const long long n0 = launch_count();
     cudaError_t ev = vcycle_level(0, r[0], z[0]);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s, &g);
     h->capsink = nullptr;
+    // kernels recorded during the capture did not run; each replay runs them all
+    graph_kernels = (int)(launch_count() - n0);
+    note_launch(-graph_kernels);
     if (ev != cudaSuccess) { if (g) cudaGraphDestroy(g); return ev; }
     if (e != cudaSuccess) return e;
     graph = g;
     CKE(cudaGraphInstantiate(&graph_exec, graph, 0));
     graph_timing = h->timing;
   }
-  return cudaGraphLaunch(graph_exec, s);
+  CKE(cudaGraphLaunch(graph_exec, s));
+  note_launch(graph_kernels);
+  return cudaSuccess;
 }
 
 template <typename T>

@@ -43,6 +43,7 @@ struct MG {
   cudaGraphExec_t graph_exec = nullptr;
   bool use_graph = true;
   bool graph_timing = false;         // the captured graph contains timer event nodes
+  int graph_kernels = 0;             // kernel launches recorded in the graph (counted per replay)
   std::vector<CapSpan> gspans;       // timer spans inside the captured graph
   void drop_graph();
   cudaError_t vcycle_graph();        // z[0] = B^{-1} r[0] through the captured graph
@@ -69,6 +70,7 @@ template <typename T>
 cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
                         const T* res, T* d, double omega, double omega_p, int color, cudaStream_t s);
 size_t vanka_patch_size(const Level& lv);            // m_st
+size_t vanka_inv_entries(const Level& lv);           // stored entries of one patch inverse (padded columns)
 size_t vanka_elem_size(const Level& lv, int which);  // entries per cell of EA (0), EB (1), EM (2)
 bool vanka_supported(const Level& lv, size_t esize);
 

@@ -45,6 +45,13 @@ void* Handle::dalloc(size_t bytes) {
   return p;
 }
 
+void Handle::upload(void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return;
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) { cudaGetLastError(); throw CudaFailure(e); }
+}
+
 Handle::~Handle() {
   for (void* p : allocs) cudaFree(p);
 }
@@ -63,8 +70,8 @@ static void build_level(Handle* h, Level& lv, const std::vector<double>& verts) 
   lv.verts64 = (double*)h->dalloc(verts.size() * sizeof(double));
   lv.verts32 = (float*)h->dalloc(verts.size() * sizeof(float));
   std::vector<float> v32(verts.begin(), verts.end());
-  cudaMemcpy(lv.verts64, verts.data(), verts.size() * sizeof(double), cudaMemcpyHostToDevice);
-  cudaMemcpy(lv.verts32, v32.data(), v32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  h->upload(lv.verts64, verts.data(), verts.size() * sizeof(double));
+  h->upload(lv.verts32, v32.data(), v32.size() * sizeof(float));
   lv.ncolors = 1 << lv.d;
   for (int c = 0; c < lv.ncolors; ++c) {
     ColorInfo& ci = lv.colors[c];
@@ -89,7 +96,7 @@ static void build_level(Handle* h, Level& lv, const std::vector<double>& verts) 
     }
     lv.nbcells[c] = (int)bc.size();
     lv.bcells[c] = (int*)h->dalloc(bc.size() * sizeof(int));
-    if (!bc.empty()) cudaMemcpy(lv.bcells[c], bc.data(), bc.size() * sizeof(int), cudaMemcpyHostToDevice);
+    h->upload(lv.bcells[c], bc.data(), bc.size() * sizeof(int));
   }
 }
 
@@ -159,7 +166,8 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
     tot += 5.0 * nst[l] * es;                                            // level vectors
     if (l + 1 < lv.size()) {
       double nl = std::pow(lr + 2.0, d), mv = d * nl, m = (lk + 1.0) * (mv + npc);
-      tot += p->vanka_fp16 ? cells * (m * m * 2.0 + 4.0) : cells * m * m * es;  // patch inverses
+      const double ms = std::ceil(m / 8.0) * 8.0;                        // padded column stride
+      tot += p->vanka_fp16 ? cells * (m * ms * 2.0 + 4.0) : cells * m * ms * es;  // patch inverses
       ea = std::max(ea, cells * mv * mv); eb = std::max(eb, cells * npc * mv); em = std::max(em, cells * nl * nl);
       nvmax = std::max(nvmax, Nv);
       tot += 3.0 * std::max((lk + 1.0) * Nv, (lk + 1.0) * Np) * es;      // transfer scratch
@@ -241,10 +249,14 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
     }
   } catch (const std::bad_alloc&) {
     return STMG_ERR_OOM;
+  } catch (const CudaFailure&) {
+    return STMG_ERR_CUDA;
   } catch (const std::exception&) {
     return STMG_ERR_ARG;
   }
-  if (cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); return STMG_ERR_CUDA; }
+  // only this handle's stream: a device-wide synchronisation would break graph captures that
+  // other handles (serving workers) may have open on their streams
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) { cudaGetLastError(); return STMG_ERR_CUDA; }
   *out = reinterpret_cast<stmg_handle*>(h.release());
   return STMG_OK;
 }

@@ -23,10 +23,10 @@ static Csr1D upload_csr(Handle* h, int rows, int cols, const std::vector<std::ve
   c.col = (int*)h->dalloc(ci.size() * sizeof(int));
   c.val64 = (double*)h->dalloc(v.size() * sizeof(double));
   c.val32 = (float*)h->dalloc(v.size() * sizeof(float));
-  cudaMemcpy(c.rowptr, rp.data(), rp.size() * sizeof(int), cudaMemcpyHostToDevice);
-  cudaMemcpy(c.col, ci.data(), ci.size() * sizeof(int), cudaMemcpyHostToDevice);
-  cudaMemcpy(c.val64, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
-  cudaMemcpy(c.val32, v32.data(), v32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  h->upload(c.rowptr, rp.data(), rp.size() * sizeof(int));
+  h->upload(c.col, ci.data(), ci.size() * sizeof(int));
+  h->upload(c.val64, v.data(), v.size() * sizeof(double));
+  h->upload(c.val32, v32.data(), v32.size() * sizeof(float));
   return c;
 }
 
@@ -112,8 +112,8 @@ void build_transfer(Handle* h, Transfer& tr, const Level& f, const Level& c, siz
   std::vector<float> PT32(PT.begin(), PT.end());
   tr.PT64 = (double*)h->dalloc(PT.size() * sizeof(double));
   tr.PT32 = (float*)h->dalloc(PT.size() * sizeof(float));
-  cudaMemcpy(tr.PT64, PT.data(), PT.size() * sizeof(double), cudaMemcpyHostToDevice);
-  cudaMemcpy(tr.PT32, PT32.data(), PT32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  h->upload(tr.PT64, PT.data(), PT.size() * sizeof(double));
+  h->upload(tr.PT32, PT32.data(), PT32.size() * sizeof(float));
   // scratch: largest intermediate = (max k + 1) * d * max(N1f^d, ...) or the pressure part
   int64_t big = (int64_t)(f.k + 1) * f.Nv;
   int64_t pbig = (int64_t)(f.k + 1) * f.Np;

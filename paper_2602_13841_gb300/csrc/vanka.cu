@@ -92,24 +92,37 @@ cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar
   return cudaErrorNotSupported;
 }
 
+template <typename T, typename SI, int D, int N>
+static void apply_rows(const Level& lv, const Problem& pb, const SI* inv, const float* scale, const T* res, T* d,
+                       double omega, double omega_p, const ColorInfo& ci, cudaStream_t s) {
+  // threads per cell: the patch rows at RR rows per thread, rounded up to whole warps; cells
+  // per block: as many as fit 128 threads (at least one)
+  const int m = (int)vanka_patch_size(lv), mr = (m + 1) & ~1;
+  const int rows = (m + InvRows<SI>::RR - 1) / InvRows<SI>::RR;
+  const int tpc = ((rows + 31) / 32) * 32;
+  const int cpb = tpc >= 128 ? 1 : 128 / tpc;
+  const size_t smem = (size_t)cpb * (mr * sizeof(T) + m * sizeof(int64_t));
+  const unsigned blocks = (unsigned)((ci.count + cpb - 1) / cpb);
+  k_vanka_apply<T, SI, D, N><<<blocks, tpc * cpb, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, scale, res, d,
+                                                             (T)omega, (T)omega_p, lv.k + 1, lv.npc, tpc, ci);
+}
+
 template <typename T, int D, int N>
 static cudaError_t apply_dn(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
                             const T* res, T* d, double omega, double omega_p, int color, cudaStream_t s) {
   const ColorInfo& ci = lv.colors[color];
   if (ci.count == 0) return cudaSuccess;
-  const int m = (int)vanka_patch_size(lv);
-  int threads = ((m + 31) / 32) * 32;
-  if (threads > 256) threads = 256;
-  size_t smem = sizeof(T) * (((m + 1) & ~1)) + sizeof(int64_t) * m + 16;
   if (invh)
-    k_vanka_apply<T, __half, D, N><<<ci.count, threads, smem, s>>>(level_args<T>(lv, pb, 0.0), (const __half*)invh,
-                                                                   scale, res, d, (T)omega, (T)omega_p, lv.k + 1,
-                                                                   lv.npc, ci);
+    apply_rows<T, __half, D, N>(lv, pb, (const __half*)invh, scale, res, d, omega, omega_p, ci, s);
   else
-    k_vanka_apply<T, T, D, N><<<ci.count, threads, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, nullptr, res, d,
-                                                              (T)omega, (T)omega_p, lv.k + 1, lv.npc, ci);
+    apply_rows<T, T, D, N>(lv, pb, inv, nullptr, res, d, omega, omega_p, ci, s);
   note_launch();
   return cudaGetLastError();
+}
+
+size_t vanka_inv_entries(const Level& lv) {
+  const size_t m = vanka_patch_size(lv);
+  return m * (size_t)inv_stride((int)m);
 }
 
 template <typename T>

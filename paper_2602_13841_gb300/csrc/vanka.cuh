@@ -35,6 +35,9 @@ struct VankaArgs {
   int* status;          // set to 1 on a zero pivot
 };
 
+// Column stride of a stored patch inverse: m rounded up to 8 entries (16-byte aligned columns).
+__host__ __device__ inline int inv_stride(int m) { return (m + 7) & ~7; }
+
 // max |x| over the block (all threads receive it)
 template <typename T>
 __device__ inline T block_absmax(T v) {
@@ -419,72 +422,124 @@ __global__ void k_patch(VankaArgs<T> V, Tab<T> tb, int64_t ncells) {
     const float sc = mx > 0 ? (float)mx : 1.f;
     const T isc = (T)1 / (T)sc;
     if (tid == 0) V.scale[cell] = sc;
-    __half* inv = V.invh + cell * (int64_t)m * m;
-    for (int ent = tid; ent < m * m; ent += nt) {
-      const int j = ent / m, i = ent % m;
-      inv[ent] = __float2half_rn((float)(S[i * m + j] * isc));
+    const int ms = inv_stride(m);
+    __half* inv = V.invh + cell * (int64_t)m * ms;
+    for (int ent = tid; ent < m * ms; ent += nt) {
+      const int j = ent / ms, i = ent % ms;
+      inv[ent] = __float2half_rn(i < m ? (float)(S[i * m + j] * isc) : 0.f);
     }
     return;
   }
-  T* inv = V.inv + cell * (int64_t)m * m;
-  for (int ent = tid; ent < m * m; ent += nt) {
-    const int j = ent / m, i = ent % m;          // column-major store: inv[j][i] = S^{-1}[i][j]
-    inv[ent] = S[i * m + j];
+  const int ms = inv_stride(m);
+  T* inv = V.inv + cell * (int64_t)m * ms;
+  for (int ent = tid; ent < m * ms; ent += nt) {
+    const int j = ent / ms, i = ent % ms;        // column-major store: inv[j][i] = S^{-1}[i][j]
+    inv[ent] = i < m ? S[i * m + j] : (T)0;      // rows m..ms-1 pad the column to 16 bytes
   }
 }
 
 // ---------------------------------------------------------------------------- sweep
-// d[patch] += omega * S~^{-1} res[patch] for the cells of one colour (one block per cell).
-// The inverse is stored in SI (T, or FP16 scaled per cell by scale[cell]); accumulation in T.
-__device__ __forceinline__ float ld_inv(const __half* p) { return __half2float(__ldg(p)); }
-__device__ __forceinline__ float ld_inv(const float* p) { return __ldg(p); }
-__device__ __forceinline__ double ld_inv(const double* p) { return __ldg(p); }
+// d[patch] += omega * S~^{-1} res[patch] for the cells of one colour.
+//
+// The inverse of a patch is stored column-major with a padded column stride ms = inv_stride(m)
+// in SI = T, or in FP16 scaled per cell by scale[cell].  TPC threads (a multiple of 32) serve
+// one cell and a block holds blockDim / TPC cells.  A thread owns RR consecutive rows (1 for T,
+// 2 for FP16: one 4-byte load per column either way, so FP16 halves the bytes at the same
+// instruction count) and keeps kApplyUnroll column loads in flight before their FMAs; the
+// threads of a cell read each column as one contiguous segment.  Accumulation in T.
+constexpr int kApplyUnroll = 8;
+
+template <typename SI> struct InvRows;
+template <> struct InvRows<float> {
+  static constexpr int RR = 1;
+  using raw = float;
+  __device__ static raw ld(const float* p) { return __ldg(p); }
+  __device__ static void get(raw v, float* o) { o[0] = v; }
+};
+template <> struct InvRows<double> {
+  static constexpr int RR = 1;
+  using raw = double;
+  __device__ static raw ld(const double* p) { return __ldg(p); }
+  __device__ static void get(raw v, double* o) { o[0] = v; }
+};
+template <> struct InvRows<__half> {
+  static constexpr int RR = 2;
+  using raw = __half2;
+  __device__ static raw ld(const __half* p) { return __ldg(reinterpret_cast<const __half2*>(p)); }
+  __device__ static void get(raw v, float* o) { const float2 f = __half22float2(v); o[0] = f.x; o[1] = f.y; }
+};
+template <typename SI> struct InvVal { using type = SI; };
+template <> struct InvVal<__half> { using type = float; };
 
 template <typename T, typename SI, int D, int N>
 __global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const float* __restrict__ scale,
                               const T* __restrict__ res, T* __restrict__ d, T omega, T omega_p, int kp1, int npc,
-                              ColorInfo ci) {
+                              int tpc, ColorInfo ci) {
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
-  const int m = kp1 * (MV + npc);
+  constexpr int RR = InvRows<SI>::RR;
+  using V = typename InvVal<SI>::type;
+  using W = typename InvRows<SI>::raw;
+  const int m = kp1 * (MV + npc), ms = inv_stride(m), mr = (m + 1) & ~1;
+  const int cpb = blockDim.x / tpc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* r = reinterpret_cast<T*>(smem_raw);
-  int64_t* gidx = reinterpret_cast<int64_t*>(r + ((m + 1) & ~1));
-  const int cidx = blockIdx.x;
-  if (cidx >= ci.count) return;
-  int cc[3] = {0, 0, 0};
-  decode_color_cell<D>(ci, cidx, cc);
-  int64_t cell = 0, s = 1;
-  for (int l = 0; l < D; ++l) { cell += (int64_t)cc[l] * s; s *= L.n; }
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int l = tid; l < m; l += nt) {
-    int64_t g;
-    if (l < kp1 * MV) {
-      const int a = l / MV, rv = l % MV, c = rv / NL, i = rv % NL;
-      g = (int64_t)a * L.Nv + c * L.nnodes + global_node<D>(L.N1, cc, N - 1, i, N);
-    } else {
-      const int a = (l - kp1 * MV) / npc, pm = (l - kp1 * MV) % npc;
-      g = (int64_t)kp1 * L.Nv + (int64_t)a * L.Np + cell * npc + pm;
+  const int slot = threadIdx.x / tpc, tid = threadIdx.x % tpc;
+  T* r = reinterpret_cast<T*>(smem_raw) + slot * mr;
+  int64_t* gidx = reinterpret_cast<int64_t*>(reinterpret_cast<T*>(smem_raw) + cpb * mr) + slot * m;
+  const int cidx = blockIdx.x * cpb + slot;
+  const bool active = cidx < ci.count;
+  int64_t cell = 0;
+  if (active) {
+    int cc[3] = {0, 0, 0};
+    decode_color_cell<D>(ci, cidx, cc);
+    int64_t s = 1;
+    for (int l = 0; l < D; ++l) { cell += (int64_t)cc[l] * s; s *= L.n; }
+    for (int l = tid; l < m; l += tpc) {
+      int64_t g;
+      if (l < kp1 * MV) {
+        const int a = l / MV, rv = l % MV, c = rv / NL, i = rv % NL;
+        g = (int64_t)a * L.Nv + c * L.nnodes + global_node<D>(L.N1, cc, N - 1, i, N);
+      } else {
+        const int a = (l - kp1 * MV) / npc, pm = (l - kp1 * MV) % npc;
+        g = (int64_t)kp1 * L.Nv + (int64_t)a * L.Np + cell * npc + pm;
+      }
+      gidx[l] = g;
+      r[l] = res[g];
     }
-    gidx[l] = g;
-    r[l] = res[g];
   }
   __syncthreads();
-  const SI* Sinv = inv + cell * (int64_t)m * m;
-  const T sc = scale ? (T)scale[cell] : (T)1;
-  for (int i = tid; i < m; i += nt) {
-    // four independent accumulators keep several column loads in flight per thread
-    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    const SI* col = Sinv + i;
-    int j = 0;
-    for (; j + 3 < m; j += 4) {
-      a0 += (T)ld_inv(col + (int64_t)j * m) * r[j];
-      a1 += (T)ld_inv(col + (int64_t)(j + 1) * m) * r[j + 1];
-      a2 += (T)ld_inv(col + (int64_t)(j + 2) * m) * r[j + 2];
-      a3 += (T)ld_inv(col + (int64_t)(j + 3) * m) * r[j + 3];
+  const int i0 = tid * RR;
+  if (!active || i0 >= m) return;
+  const SI* col = inv + cell * (int64_t)m * ms + i0;
+  T acc[RR];
+#pragma unroll
+  for (int t = 0; t < RR; ++t) acc[t] = 0;
+  int j = 0;
+  for (; j + kApplyUnroll <= m; j += kApplyUnroll) {
+    W w[kApplyUnroll];
+#pragma unroll
+    for (int u = 0; u < kApplyUnroll; ++u) w[u] = InvRows<SI>::ld(col + (int64_t)(j + u) * ms);
+#pragma unroll
+    for (int u = 0; u < kApplyUnroll; ++u) {
+      V v[RR];
+      InvRows<SI>::get(w[u], v);
+      const T ru = r[j + u];
+#pragma unroll
+      for (int t = 0; t < RR; ++t) acc[t] += (T)v[t] * ru;
     }
-    for (; j < m; ++j) a0 += (T)ld_inv(col + (int64_t)j * m) * r[j];
-    d[gidx[i]] += (i < kp1 * MV ? omega : omega_p) * sc * ((a0 + a1) + (a2 + a3));
+  }
+  for (; j < m; ++j) {
+    V v[RR];
+    InvRows<SI>::get(InvRows<SI>::ld(col + (int64_t)j * ms), v);
+    const T rj = r[j];
+#pragma unroll
+    for (int t = 0; t < RR; ++t) acc[t] += (T)v[t] * rj;
+  }
+  const T sc = scale ? (T)scale[cell] : (T)1;
+#pragma unroll
+  for (int t = 0; t < RR; ++t) {
+    const int i = i0 + t;
+    if (i < m) d[gidx[i]] += (i < kp1 * MV ? omega : omega_p) * sc * acc[t];
   }
 }
 
