@@ -194,6 +194,12 @@ typedef struct {
  * rest of multigrid, other) during stmg_slab_solve (adds a few event records per phase). */
 stmg_status stmg_set_timing(stmg_handle* h, int on);
 
+/* Restrict the per-kernel-class timers of stmg_set_timing to the classes whose bit is set in
+ * mask (bit c = class c of stmg_kernel_profile; default: all).  Every timed launch adds two
+ * event records (graph nodes inside the captured V-cycle), so timing one class perturbs the
+ * solve less than timing all of them; the phase times are recorded either way. */
+stmg_status stmg_set_timing_classes(stmg_handle* h, unsigned mask);
+
 /* Device time (ms), launches and algorithmic bytes accumulated per kernel class while timing is
  * on (collected at the end of each stmg_slab_solve).  Classes: 0 FP64 Jacobian apply (outer
  * FGMRES), 1 preconditioner-precision Jacobian apply (level residuals), 2 residual, 3 Vanka

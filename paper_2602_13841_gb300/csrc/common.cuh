@@ -23,6 +23,35 @@ struct Tab {
   int k, npc, r;
 };
 
+// Time diagonalisation of the Vanka patch for a slab of length tau (see LevelTables): block e
+// has eigenvalue lam_e = (2/tau) mu_e of W^{-1} K, forward row F[e][a] = (2/tau) (Q^{-1}
+// Omega^{-1})[e][a] and backward column G[a][e] (x2 for a complex block, whose conjugate
+// partner is implied: y_a = sum_e Re(G[a][e] yhat_e)).
+template <typename T>
+struct TEig {
+  int nblk;
+  int cplx[MAXKP1], off[MAXKP1];
+  T lre[MAXKP1], lim[MAXKP1];
+  T Fre[MAXKP1][MAXKP1], Fim[MAXKP1][MAXKP1];
+  T Gre[MAXKP1][MAXKP1], Gim[MAXKP1][MAXKP1];
+};
+
+template <typename T>
+TEig<T> make_teig(const LevelTables& L, double tau) {
+  TEig<T> t{};
+  const double s = 2.0 / tau;
+  t.nblk = L.tnblk;
+  for (int b = 0; b < MAXKP1; ++b) {
+    t.cplx[b] = L.tcplx[b]; t.off[b] = L.toff[b];
+    t.lre[b] = (T)(s * L.tmu_re[b]); t.lim[b] = (T)(s * L.tmu_im[b]);
+    for (int a = 0; a < MAXKP1; ++a) {
+      t.Fre[b][a] = (T)(s * L.tF_re[b][a]); t.Fim[b][a] = (T)(s * L.tF_im[b][a]);
+      t.Gre[a][b] = (T)L.tG_re[a][b]; t.Gim[a][b] = (T)L.tG_im[a][b];
+    }
+  }
+  return t;
+}
+
 template <typename T>
 Tab<T> make_tab(const LevelTables& L, double tau) {
   Tab<T> t{};

@@ -63,14 +63,16 @@ struct Handle {
   // nodes) and go to `capsink`; they are read after every replay of that graph.
   std::vector<CapSpan>* capsink = nullptr;
   cudaEvent_t cap_open[8] = {};
+  unsigned kmask = ~0u;               // kernel classes that record timer spans
+  bool ktimed(int cls) const { return timing && ((kmask >> cls) & 1u); }
   void kbegin(int cls) {
-    if (!timing) return;
+    if (!ktimed(cls)) return;
     // external event-record nodes: the graph records these events at every replay
     if (capsink) { cudaEventCreate(&cap_open[cls]); cudaEventRecordWithFlags(cap_open[cls], stream, cudaEventRecordExternal); }
     else kt[cls].begin(stream);
   }
   void kend(int cls, double bytes = 0.0, int launches = 1) {
-    if (!timing) return;
+    if (!ktimed(cls)) return;
     if (capsink) {
       cudaEvent_t e; cudaEventCreate(&e); cudaEventRecordWithFlags(e, stream, cudaEventRecordExternal);
       capsink->push_back({cls, cap_open[cls], e, bytes, launches});

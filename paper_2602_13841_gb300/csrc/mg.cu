@@ -31,7 +31,7 @@ cudaError_t MG<T>::allocate(Handle* hh) {
         size_t m = vanka_patch_size(lv);
         if (h->prm.vanka_fp16) {
           invh[l] = h->dalloc((size_t)(lv.Np / lv.npc) * vanka_inv_entries(lv) * 2);
-          iscale[l] = (float*)h->dalloc((size_t)(lv.Np / lv.npc) * sizeof(float));
+          iscale[l] = (float*)h->dalloc((size_t)(lv.Np / lv.npc) * (lv.k + 1) * sizeof(float));
         } else {
           inv[l] = (T*)h->dalloc((size_t)(lv.Np / lv.npc) * vanka_inv_entries(lv) * sizeof(T));
         }
@@ -49,6 +49,7 @@ cudaError_t MG<T>::allocate(Handle* hh) {
       vstar = (T*)h->dalloc(nv * sizeof(T));
     }
     status = (int*)h->dalloc(sizeof(int));
+    wstat = (int*)h->dalloc(sizeof(int));
     tr.resize(nl > 0 ? nl - 1 : 0);
     for (int l = 0; l + 1 < nl; ++l) build_transfer(h, tr[l], h->levels[l], h->levels[l + 1], sizeof(T));
     const Level& c = h->levels[nl - 1];
@@ -79,11 +80,21 @@ __global__ void k_identity(double* I, int n) {
 }
 
 template <typename T>
+cudaError_t MG<T>::check_wait() {
+  int v = 0;
+  CKE(cudaMemcpyAsync(&v, wstat, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CKE(cudaMemsetAsync(wstat, 0, sizeof(int), h->stream));
+  CKE(cudaStreamSynchronize(h->stream));
+  return v ? cudaErrorTimeout : cudaSuccess;
+}
+
+template <typename T>
 cudaError_t MG<T>::setup(const double* U64) {
   cudaStream_t s = h->stream;
   const Level& f = h->levels[0];
   if (!smoothable) return cudaErrorNotSupported;
   CKE(cudaMemsetAsync(status, 0, sizeof(int), s));
+  CKE(cudaMemsetAsync(wstat, 0, sizeof(int), s));
   CKE((vcopy<double, T>(f.Nst, U64, U[0], s)));
   for (int l = 0; l + 1 < nl; ++l) {
     const Level& c = h->levels[l + 1];
@@ -148,12 +159,14 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
     }
     // one timer span over the colour launches of the sweep (they run back to back);
     // algorithmic bytes: the patch inverses of every cell, residual gather, d read and write
-    const double m = (double)vanka_patch_size(lv);
-    const double ib = invh[l] ? m * m * 2.0 + 4.0 : m * m * sizeof(T);
+    // per cell: (k+1) m_s^2 stored reals (one spatial inverse per real time eigenvalue, a complex
+    // one per conjugate pair), residual gather and d update on the (k+1) m_s patch DoFs
+    const double ms = (double)vanka_spatial_size(lv), m = (double)vanka_patch_size(lv);
+    const double ib = (lv.k + 1) * ms * ms * (invh[l] ? 2.0 : (double)sizeof(T)) + (invh[l] ? 4.0 * (lv.k + 1) : 0.0);
     int64_t cells = 0;
     h->kbegin(KC_VANKA_APPLY);
     for (int c = 0; c < lv.ncolors; ++c) {
-      CKE(vanka_apply<T>(lv, h->pb, inv[l], invh[l], iscale[l], res, d, omega, h->prm.omega_p, c, s));
+      CKE(vanka_apply<T>(lv, h->pb, inv[l], invh[l], iscale[l], res, d, omega, h->prm.omega_p, c, wstat, s));
       cells += lv.colors[c].count;
     }
     h->kend(KC_VANKA_APPLY, (double)cells * (ib + 3.0 * m * sizeof(T)), lv.ncolors);
@@ -200,7 +213,7 @@ void MG<T>::drop_graph() {
 template <typename T>
 cudaError_t MG<T>::vcycle_graph() {
   cudaStream_t s = h->stream;
-  if (graph_exec && graph_timing != h->timing) drop_graph();
+  if (graph_exec && (graph_timing != h->timing || graph_kmask != h->kmask)) drop_graph();
   if (!graph_exec) {
     // capture the V-cycle on r[0] -> z[0]; all buffers and parameters are fixed per handle, so
     // the graph stays valid across smoother rebuilds
@@ -221,6 +234,7 @@ cudaError_t MG<T>::vcycle_graph() {
     graph = g;
     CKE(cudaGraphInstantiate(&graph_exec, graph, 0));
     graph_timing = h->timing;
+    graph_kmask = h->kmask;
   }
   CKE(cudaGraphLaunch(graph_exec, s));
   note_launch(graph_kernels);

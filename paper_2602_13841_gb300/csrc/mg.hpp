@@ -27,6 +27,8 @@ struct MG {
   std::vector<Transfer> tr;
   T *EA = nullptr, *EB = nullptr, *EM = nullptr, *vstar = nullptr;
   int* status = nullptr;             // device flag: zero pivot in a patch
+  int* wstat = nullptr;              // device flag: a bounded wait in the Vanka apply ran out
+  cudaError_t check_wait();          // reads and clears wstat (synchronises the stream)
   // coarsest level: bordered Jacobian (FP64), its FP32 inverse, FP64 refinement buffers
   int Nc = 0, Nb = 0;
   double *A64 = nullptr, *Ucs = nullptr, *cb = nullptr, *cx = nullptr, *cr = nullptr, *cw = nullptr;
@@ -42,7 +44,8 @@ struct MG {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   bool use_graph = true;
-  bool graph_timing = false;         // the captured graph contains timer event nodes
+  bool graph_timing = false;         // the captured graph contains timer event nodes ...
+  unsigned graph_kmask = ~0u;        // ... of these kernel classes
   int graph_kernels = 0;             // kernel launches recorded in the graph (counted per replay)
   std::vector<CapSpan> gspans;       // timer spans inside the captured graph
   void drop_graph();
@@ -68,9 +71,10 @@ cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar
 // inv: patch inverses of precision T, or (invh non-null) FP16 inverses scaled by scale[cell].
 template <typename T>
 cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
-                        const T* res, T* d, double omega, double omega_p, int color, cudaStream_t s);
-size_t vanka_patch_size(const Level& lv);            // m_st
-size_t vanka_inv_entries(const Level& lv);           // stored entries of one patch inverse (padded columns)
+                        const T* res, T* d, double omega, double omega_p, int color, int* wstat, cudaStream_t s);
+size_t vanka_spatial_size(const Level& lv);          // m_s = d (r+2)^d + npc
+size_t vanka_patch_size(const Level& lv);            // m_st = (k+1) m_s
+size_t vanka_inv_entries(const Level& lv);           // stored reals of one cell's patch inverse ((k+1) m_s x stride)
 size_t vanka_elem_size(const Level& lv, int which);  // entries per cell of EA (0), EB (1), EM (2)
 bool vanka_supported(const Level& lv, size_t esize);
 

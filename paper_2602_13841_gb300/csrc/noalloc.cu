@@ -57,7 +57,7 @@ static cudaError_t sweep_noalloc(Handle* h, MG<T>& mg, int l, const T* rhs, T* d
     }
     for (int c = 0; c < lv.ncolors; ++c) {
       cudaError_t e = vanka_apply<T>(lv, h->pb, mg.inv[l], mg.invh[l], mg.iscale[l], res, d, h->prm.omega,
-                                     h->prm.omega_p, c, s);
+                                     h->prm.omega_p, c, mg.wstat, s);
       if (e != cudaSuccess) return e;
     }
   }
@@ -90,6 +90,9 @@ extern "C" stmg_status stmg_smoother_sweep_noalloc(stmg_handle* hh, int level, c
   e = fp32 ? sweep_noalloc<float>(h, *h->mg32, level, (const float*)rhs, (float*)d, nsweeps, zero_start != 0, (float*)q)
            : sweep_noalloc<double>(h, *h->mg64, level, (const double*)rhs, (double*)d, nsweeps, zero_start != 0,
                                    (double*)q);
+  if (e == cudaSuccess) e = fp32 ? h->mg32->check_wait() : h->mg64->check_wait();
+  if (e == cudaErrorTimeout)
+    return h->fail(STMG_ERR_TIMEOUT, "smoother_sweep_noalloc: a bounded wait in the Vanka apply ran out");
   if (e != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string("smoother_sweep_noalloc: ") + cudaGetErrorString(e));
   return STMG_OK;
 }

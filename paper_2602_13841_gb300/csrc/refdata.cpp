@@ -2,7 +2,10 @@
 // bisection, which is robust for the low degrees used here (<= 6).
 #include "refdata.hpp"
 
+#include <algorithm>
 #include <cmath>
+#include <complex>
+#include <utility>
 #include <stdexcept>
 
 namespace stmg {
@@ -118,6 +121,138 @@ double lagrange_d(const std::vector<double>& nodes, int i, double x) {
   return s;
 }
 
+using cplx = std::complex<double>;
+
+// Roots of z^3 + a2 z^2 + a1 z + a0 (Durand-Kerner iteration, then Newton polishing).
+static void cubic_roots(cplx a2, cplx a1, cplx a0, cplx z[3]) {
+  auto f = [&](cplx x) { return ((x + a2) * x + a1) * x + a0; };
+  auto df = [&](cplx x) { return (3.0 * x + 2.0 * a2) * x + a1; };
+  const cplx seed(0.4, 0.9);
+  z[0] = 1.0; z[1] = seed; z[2] = seed * seed;
+  for (int it = 0; it < 500; ++it)
+    for (int i = 0; i < 3; ++i) {
+      cplx den = 1.0;
+      for (int j = 0; j < 3; ++j) if (j != i) den *= (z[i] - z[j]);
+      z[i] -= f(z[i]) / den;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int it = 0; it < 3; ++it) { cplx g = df(z[i]); if (std::abs(g) > 0) z[i] -= f(z[i]) / g; }
+}
+
+// Eigen-decomposition of the (k+1) x (k+1) matrix P = Omega^{-1} K.  Its eigenvalues are
+// distinct: k = 0 one real, k = 1 one conjugate pair, k = 2 one pair and one real.
+static void time_eigen(LevelTables& T) {
+  const int n = T.k + 1;
+  double P[3][3] = {};
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) P[a][b] = T.K[a][b] / T.omega[a];
+  cplx lam[3], Q[3][3];
+  if (n == 1) {
+    lam[0] = P[0][0]; Q[0][0] = 1.0;
+  } else if (n == 2) {
+    const double tr = P[0][0] + P[1][1], det = P[0][0] * P[1][1] - P[0][1] * P[1][0];
+    const cplx sq = std::sqrt(cplx(0.25 * tr * tr - det, 0.0));
+    lam[0] = 0.5 * tr + sq; lam[1] = 0.5 * tr - sq;
+    for (int e = 0; e < 2; ++e) {
+      cplx v0 = P[0][1], v1 = lam[e] - P[0][0];
+      if (std::abs(v0) + std::abs(v1) < 1e-14) { v0 = lam[e] - P[1][1]; v1 = P[1][0]; }
+      const double nv = std::sqrt(std::norm(v0) + std::norm(v1));
+      Q[0][e] = v0 / nv; Q[1][e] = v1 / nv;
+    }
+  } else {
+    const double tr = P[0][0] + P[1][1] + P[2][2];
+    const double m2 = P[0][0] * P[1][1] - P[0][1] * P[1][0] + P[0][0] * P[2][2] - P[0][2] * P[2][0] +
+                      P[1][1] * P[2][2] - P[1][2] * P[2][1];
+    const double det = P[0][0] * (P[1][1] * P[2][2] - P[1][2] * P[2][1]) -
+                       P[0][1] * (P[1][0] * P[2][2] - P[1][2] * P[2][0]) +
+                       P[0][2] * (P[1][0] * P[2][1] - P[1][1] * P[2][0]);
+    cubic_roots(-tr, m2, -det, lam);
+    for (int e = 0; e < 3; ++e) {
+      // null vector of P - lam I: the largest cross product of two of its rows
+      cplx R[3][3];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) R[a][b] = P[a][b] - (a == b ? lam[e] : cplx(0.0));
+      cplx best[3]; double bn = -1;
+      const int pr[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+      for (auto& q : pr) {
+        const cplx* u = R[q[0]]; const cplx* v = R[q[1]];
+        cplx c[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+        const double nc = std::norm(c[0]) + std::norm(c[1]) + std::norm(c[2]);
+        if (nc > bn) { bn = nc; best[0] = c[0]; best[1] = c[1]; best[2] = c[2]; }
+      }
+      const double nv = std::sqrt(bn);
+      for (int a = 0; a < 3; ++a) Q[a][e] = best[a] / nv;
+    }
+  }
+  // real eigenvalues get real eigenvectors; a conjugate partner gets the conjugate column
+  bool used[3] = {false, false, false};
+  int blk_of[3] = {-1, -1, -1};
+  T.tnblk = 0;
+  int unit = 0;
+  for (int e = 0; e < n; ++e) {
+    if (used[e]) continue;
+    const double scale = std::max(1.0, std::abs(lam[e]));
+    const bool real = std::abs(lam[e].imag()) <= 1e-10 * scale;
+    const int b = T.tnblk++;
+    used[e] = true;
+    if (real) {
+      lam[e] = lam[e].real();
+      double nv = 0;
+      for (int a = 0; a < n; ++a) nv += Q[a][e].real() * Q[a][e].real();
+      // a real null vector is a complex multiple of its real part (or imaginary part)
+      if (nv < 1e-20) for (int a = 0; a < n; ++a) Q[a][e] = Q[a][e].imag();
+      else for (int a = 0; a < n; ++a) Q[a][e] = Q[a][e].real();
+      nv = 0;
+      for (int a = 0; a < n; ++a) nv += std::norm(Q[a][e]);
+      for (int a = 0; a < n; ++a) Q[a][e] /= std::sqrt(nv);
+      T.tcplx[b] = 0; T.toff[b] = unit; unit += 1;
+      blk_of[e] = b;
+    } else {
+      int f = -1;
+      for (int g = 0; g < n; ++g)
+        if (!used[g] && std::abs(lam[g] - std::conj(lam[e])) <= 1e-8 * scale) { f = g; break; }
+      if (f < 0) throw std::runtime_error("time matrix: unpaired complex eigenvalue");
+      used[f] = true;
+      const int rep = lam[e].imag() > 0 ? e : f, par = rep == e ? f : e;
+      lam[par] = std::conj(lam[rep]);
+      for (int a = 0; a < n; ++a) Q[a][par] = std::conj(Q[a][rep]);
+      T.tcplx[b] = 1; T.toff[b] = unit; unit += 2;
+      blk_of[rep] = b;
+    }
+  }
+  // Q^{-1} by Gauss-Jordan with partial pivoting (n <= 3)
+  cplx A[3][6];
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < 2 * n; ++b) A[a][b] = b < n ? Q[a][b] : cplx(b - n == a ? 1.0 : 0.0);
+  for (int p = 0; p < n; ++p) {
+    int piv = p;
+    for (int a = p + 1; a < n; ++a) if (std::abs(A[a][p]) > std::abs(A[piv][p])) piv = a;
+    if (std::abs(A[piv][p]) < 1e-14) throw std::runtime_error("time matrix: singular eigenvectors");
+    for (int b = 0; b < 2 * n; ++b) std::swap(A[p][b], A[piv][b]);
+    const cplx inv = 1.0 / A[p][p];
+    for (int b = 0; b < 2 * n; ++b) A[p][b] *= inv;
+    for (int a = 0; a < n; ++a)
+      if (a != p) {
+        const cplx f = A[a][p];
+        for (int b = 0; b < 2 * n; ++b) A[a][b] -= f * A[p][b];
+      }
+  }
+  for (int e = 0; e < n; ++e) {
+    const int b = blk_of[e];
+    if (b < 0) continue;
+    T.tmu_re[b] = lam[e].real();
+    T.tmu_im[b] = T.tcplx[b] ? lam[e].imag() : 0.0;
+    const double two = T.tcplx[b] ? 2.0 : 1.0;
+    for (int a = 0; a < n; ++a) {
+      const cplx f = A[e][n + a] / T.omega[a];
+      T.tF_re[b][a] = f.real();
+      T.tF_im[b][a] = T.tcplx[b] ? f.imag() : 0.0;
+      T.tG_re[a][b] = two * Q[a][e].real();
+      T.tG_im[a][b] = T.tcplx[b] ? two * Q[a][e].imag() : 0.0;
+    }
+  }
+}
+
 void LevelTables::build(int d_, int r_, int k_) {
   d = d_; r = r_; k = k_;
   n = r + 2; nq = r + 2;
@@ -171,6 +306,7 @@ void LevelTables::build(int d_, int r_, int k_) {
           s += gtw[q] * lagrange_d(tn, b, gt[q]) * lagrange(tn, a, gt[q]);
       K[a][b] = s + C[a] * C[b];
     }
+  time_eigen(*this);
 }
 
 }  // namespace stmg

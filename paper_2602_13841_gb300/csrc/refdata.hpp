@@ -41,6 +41,16 @@ struct LevelTables {
   double that[MAXKP1], omega[MAXKP1];
   double K[MAXKP1][MAXKP1], C[MAXKP1];
   double phi_mid[MAXKP1];      // phi_a at the slab midpoint (t_hat = 0)
+  // Time diagonalisation of the Vanka patch (Sec. 4.3: the spatial core of the surrogate patch
+  // is shared by all time nodes).  Omega^{-1} K = Q diag(mu) Q^{-1}, Omega = diag(omega); for a
+  // slab of length tau the patch time matrix W^{-1} K (W = tau/2 Omega) has eigenvalues
+  // (2/tau) mu and the same Q.  One block per real eigenvalue and one per complex-conjugate pair
+  // (represented by its member with Im mu > 0); tnunits = k+1 real units (complex blocks 2).
+  int tnblk = 0;
+  int tcplx[MAXKP1] = {}, toff[MAXKP1] = {};     // block is complex; first unit of the block
+  double tmu_re[MAXKP1] = {}, tmu_im[MAXKP1] = {};
+  double tF_re[MAXKP1][MAXKP1] = {}, tF_im[MAXKP1][MAXKP1] = {};   // [block][a]: row of Q^{-1} Omega^{-1}
+  double tG_re[MAXKP1][MAXKP1] = {}, tG_im[MAXKP1][MAXKP1] = {};   // [a][block]: Q column, x2 if complex
   void build(int d, int r, int k);
 };
 

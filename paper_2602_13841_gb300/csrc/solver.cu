@@ -386,6 +386,8 @@ stmg_status stmg_smoother_sweep(stmg_handle* hh, int level, const void* rhs, voi
   if (!built) return h->fail(STMG_ERR_ARG, "smoother_sweep: call stmg_smoother_build first");
   cudaError_t e = h->precond_fp32() ? h->mg32->sweep(level, (const float*)rhs, (float*)d, nsweeps, zero_start != 0)
                                     : h->mg64->sweep(level, (const double*)rhs, (double*)d, nsweeps, zero_start != 0);
+  if (e == cudaSuccess) e = h->precond_fp32() ? h->mg32->check_wait() : h->mg64->check_wait();
+  if (e == cudaErrorTimeout) return h->fail(STMG_ERR_TIMEOUT, "smoother_sweep: a bounded wait in the Vanka apply ran out");
   if (e != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string("smoother_sweep: ") + cudaGetErrorString(e));
   return STMG_OK;
 }
@@ -396,6 +398,8 @@ stmg_status stmg_vcycle(stmg_handle* hh, const double* r, double* z) {
   bool built = h->precond_fp32() ? (h->mg32 && h->mg32->built) : (h->mg64 && h->mg64->built);
   if (!built) return h->fail(STMG_ERR_ARG, "vcycle: call stmg_smoother_build first");
   cudaError_t e = h->precond_fp32() ? precondition<float>(h, *h->mg32, r, z) : precondition<double>(h, *h->mg64, r, z);
+  if (e == cudaSuccess) e = h->precond_fp32() ? h->mg32->check_wait() : h->mg64->check_wait();
+  if (e == cudaErrorTimeout) return h->fail(STMG_ERR_TIMEOUT, "vcycle: a bounded wait in the Vanka apply ran out");
   if (e != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string("vcycle: ") + cudaGetErrorString(e));
   return STMG_OK;
 }
@@ -465,6 +469,12 @@ stmg_status stmg_set_timing(stmg_handle* hh, int on) {
   return STMG_OK;
 }
 
+stmg_status stmg_set_timing_classes(stmg_handle* hh, unsigned mask) {
+  if (!hh) return STMG_ERR_ARG;
+  H(hh)->kmask = mask;
+  return STMG_OK;
+}
+
 stmg_status stmg_slab_solve(stmg_handle* hh, double t_start, const double* V_prev, double* U, stmg_stats* st) {
   if (!hh || !V_prev || !U) return STMG_ERR_ARG;
   Handle* h = H(hh);
@@ -485,6 +495,11 @@ stmg_status stmg_slab_solve(stmg_handle* hh, double t_start, const double* V_pre
   }
   stmg_status rs = h->precond_fp32() ? newton<float>(h, *h->mg32, t_start, V_prev, U, S)
                                      : newton<double>(h, *h->mg64, t_start, V_prev, U, S);
+  if (rs == STMG_OK || rs == STMG_ERR_NOT_CONVERGED) {
+    const cudaError_t w = h->precond_fp32() ? h->mg32->check_wait() : h->mg64->check_wait();
+    if (w == cudaErrorTimeout) rs = h->fail(STMG_ERR_TIMEOUT, "slab_solve: a bounded wait in the Vanka apply ran out");
+    else if (w != cudaSuccess) rs = h->fail(STMG_ERR_CUDA, std::string("slab_solve: ") + cudaGetErrorString(w));
+  }
   if (h->timing) {
     cudaEventRecord(e1, h->stream);
     cudaEventSynchronize(e1);

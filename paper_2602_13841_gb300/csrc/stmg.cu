@@ -165,9 +165,10 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
     tot += 12.0 * std::pow(ln + 1.0, d) + 4.0 * cells;                  // vertices, boundary lists
     tot += 5.0 * nst[l] * es;                                            // level vectors
     if (l + 1 < lv.size()) {
-      double nl = std::pow(lr + 2.0, d), mv = d * nl, m = (lk + 1.0) * (mv + npc);
-      const double ms = std::ceil(m / 8.0) * 8.0;                        // padded column stride
-      tot += p->vanka_fp16 ? cells * (m * ms * 2.0 + 4.0) : cells * m * ms * es;  // patch inverses
+      double nl = std::pow(lr + 2.0, d), mv = d * nl, msp = mv + npc;
+      const double st = std::ceil(msp / 8.0) * 8.0;                      // padded column stride
+      const double ent = (lk + 1.0) * msp * st;                          // time-diagonalised inverse
+      tot += p->vanka_fp16 ? cells * (ent * 2.0 + 4.0 * (lk + 1.0)) : cells * ent * es;  // patch inverses
       ea = std::max(ea, cells * mv * mv); eb = std::max(eb, cells * npc * mv); em = std::max(em, cells * nl * nl);
       nvmax = std::max(nvmax, Nv);
       tot += 3.0 * std::max((lk + 1.0) * Nv, (lk + 1.0) * Np) * es;      // transfer scratch

@@ -9,11 +9,13 @@
 
 namespace stmg {
 
-size_t vanka_patch_size(const Level& lv) {
+size_t vanka_spatial_size(const Level& lv) {
   int nl = 1;
   for (int l = 0; l < lv.d; ++l) nl *= (lv.r + 2);
-  return (size_t)(lv.k + 1) * (lv.d * nl + lv.npc);
+  return (size_t)(lv.d * nl + lv.npc);
 }
+
+size_t vanka_patch_size(const Level& lv) { return (size_t)(lv.k + 1) * vanka_spatial_size(lv); }
 
 size_t vanka_elem_size(const Level& lv, int which) {
   size_t nl = 1;
@@ -32,11 +34,11 @@ static size_t elem_smem(size_t es) {
 }
 
 static size_t patch_smem(const Level& lv, size_t es) {
-  size_t m = vanka_patch_size(lv);
+  const size_t ms = vanka_spatial_size(lv);
   size_t nl = 1;
   for (int l = 0; l < lv.d; ++l) nl *= (lv.r + 2);
-  size_t mv = lv.d * nl;
-  return es * (m * m + mv * mv + nl * nl + m) + sizeof(int) * m;
+  const size_t mv = lv.d * nl;
+  return es * (2 * ms * ms + mv * mv + nl * nl + 2 * ms) + sizeof(int) * ms + 16;
 }
 
 static size_t elem_smem_any(const Level& lv, size_t es) {
@@ -47,7 +49,9 @@ static size_t elem_smem_any(const Level& lv, size_t es) {
 
 bool vanka_supported(const Level& lv, size_t es) {
   const size_t lim = 227 * 1024;
-  return patch_smem(lv, es) <= lim && elem_smem_any(lv, es) <= lim;
+  const int ms = (int)vanka_spatial_size(lv);
+  return patch_smem(lv, es) <= lim && elem_smem_any(lv, es) <= lim &&
+         apply_smem_bytes(lv.k + 1, ms, es, es) <= lim;
 }
 
 // v* = sum_a phi_a(t*) V^a
@@ -75,7 +79,7 @@ static cudaError_t build_dn(const Level& lv, const Problem& pb, const T* U, T* v
   size_t ps = patch_smem(lv, sizeof(T));
   e = cudaFuncSetAttribute(k_patch<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
   if (e != cudaSuccess) return e;
-  k_patch<T, D, N><<<(unsigned)ncells, 256, ps, s>>>(V, tb, ncells);
+  k_patch<T, D, N><<<(unsigned)ncells, 256, ps, s>>>(V, tb, make_teig<T>(lv.tabs, pb.tau), ncells);
   note_launch(3);
   return cudaGetLastError();
 }
@@ -93,43 +97,46 @@ cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar
 }
 
 template <typename T, typename SI, int D, int N>
-static void apply_rows(const Level& lv, const Problem& pb, const SI* inv, const float* scale, const T* res, T* d,
-                       double omega, double omega_p, const ColorInfo& ci, cudaStream_t s) {
-  // threads per cell: the patch rows at RR rows per thread, rounded up to whole warps; cells
-  // per block: as many as fit 128 threads (at least one)
-  const int m = (int)vanka_patch_size(lv), mr = (m + 1) & ~1;
-  const int rows = (m + InvRows<SI>::RR - 1) / InvRows<SI>::RR;
-  const int tpc = ((rows + 31) / 32) * 32;
-  const int cpb = tpc >= 128 ? 1 : 128 / tpc;
-  const size_t smem = (size_t)cpb * (mr * sizeof(T) + m * sizeof(int64_t));
-  const unsigned blocks = (unsigned)((ci.count + cpb - 1) / cpb);
-  k_vanka_apply<T, SI, D, N><<<blocks, tpc * cpb, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, scale, res, d,
-                                                             (T)omega, (T)omega_p, lv.k + 1, lv.npc, tpc, ci);
+static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv, const float* scale, const T* res,
+                               T* d, double omega, double omega_p, const ColorInfo& ci, int* wstat,
+                               cudaStream_t s) {
+  // one block per cell, threads = spatial patch rows rounded up to whole warps
+  const int ms = (int)vanka_spatial_size(lv), kp1 = lv.k + 1;
+  const int threads = ((ms + 31) / 32) * 32;
+  const size_t smem = apply_smem_bytes(kp1, ms, sizeof(SI), sizeof(T));
+  cudaError_t e = cudaFuncSetAttribute(k_vanka_apply<T, SI, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_vanka_apply<T, SI, D, N><<<(unsigned)ci.count, threads, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, scale, res, d,
+                                                                       (T)omega, (T)omega_p, kp1, lv.npc,
+                                                                       make_teig<T>(lv.tabs, pb.tau), ci, wstat);
+  return cudaSuccess;
 }
 
 template <typename T, int D, int N>
 static cudaError_t apply_dn(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
-                            const T* res, T* d, double omega, double omega_p, int color, cudaStream_t s) {
+                            const T* res, T* d, double omega, double omega_p, int color, int* wstat,
+                            cudaStream_t s) {
   const ColorInfo& ci = lv.colors[color];
   if (ci.count == 0) return cudaSuccess;
-  if (invh)
-    apply_rows<T, __half, D, N>(lv, pb, (const __half*)invh, scale, res, d, omega, omega_p, ci, s);
-  else
-    apply_rows<T, T, D, N>(lv, pb, inv, nullptr, res, d, omega, omega_p, ci, s);
+  cudaError_t e = invh ? apply_cells<T, __half, D, N>(lv, pb, (const __half*)invh, scale, res, d, omega, omega_p, ci,
+                                                      wstat, s)
+                       : apply_cells<T, T, D, N>(lv, pb, inv, nullptr, res, d, omega, omega_p, ci, wstat, s);
+  if (e != cudaSuccess) return e;
   note_launch();
   return cudaGetLastError();
 }
 
 size_t vanka_inv_entries(const Level& lv) {
-  const size_t m = vanka_patch_size(lv);
-  return m * (size_t)inv_stride((int)m);
+  const size_t ms = vanka_spatial_size(lv);
+  return (size_t)(lv.k + 1) * ms * (size_t)inv_stride((int)ms);
 }
 
 template <typename T>
 cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
-                        const T* res, T* d, double omega, double omega_p, int color, cudaStream_t s) {
+                        const T* res, T* d, double omega, double omega_p, int color, int* wstat, cudaStream_t s) {
   const int N = lv.r + 2;
-#define STMG_A(DD, NN) return apply_dn<T, DD, NN>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, s)
+#define STMG_A(DD, NN) return apply_dn<T, DD, NN>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, wstat, s)
   if (lv.d == 2) { if (N == 3) STMG_A(2, 3); if (N == 4) STMG_A(2, 4); if (N == 5) STMG_A(2, 5); }
   else { if (N == 3) STMG_A(3, 3); if (N == 4) STMG_A(3, 4); }
 #undef STMG_A
@@ -141,8 +148,8 @@ template cudaError_t vanka_build<float>(const Level&, const Problem&, const floa
 template cudaError_t vanka_build<double>(const Level&, const Problem&, const double*, double*, double*, double*,
                                          double*, double*, void*, float*, int*, cudaStream_t);
 template cudaError_t vanka_apply<float>(const Level&, const Problem&, const float*, const void*, const float*,
-                                        const float*, float*, double, double, int, cudaStream_t);
+                                        const float*, float*, double, double, int, int*, cudaStream_t);
 template cudaError_t vanka_apply<double>(const Level&, const Problem&, const double*, const void*, const float*,
-                                         const double*, double*, double, double, int, cudaStream_t);
+                                         const double*, double*, double, double, int, int*, cudaStream_t);
 
 }  // namespace stmg

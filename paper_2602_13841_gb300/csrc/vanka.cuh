@@ -29,9 +29,12 @@ struct VankaArgs {
   T* EA;                // [cells][mv][mv]
   T* EB;                // [cells][npc][mv]
   T* EM;                // [cells][nl][nl]
-  T* inv;               // [cells][mst][mst] column-major inverse (storage in T), or
-  __half* invh;         // the same scaled to [-1, 1] in FP16 with one FP32 factor per cell
-  float* scale;         // [cells]
+  // Patch inverse of a cell, time-diagonalised: one spatial inverse T_e^{-1} (size m_s = mv +
+  // npc) per eigen-block e, column-major with padded stride inv_stride(m_s); a complex block
+  // stores (re, im) pairs.  k+1 units of m_s x stride reals per cell, storage in T, or
+  T* inv;
+  __half* invh;         // the same scaled to [-1, 1] in FP16 with one FP32 factor per block
+  float* scale;         // [cells][nblk]
   int* status;          // set to 1 on a zero pivot
 };
 
@@ -327,21 +330,112 @@ __device__ bool gauss_jordan(T* S, int m, int ld, int* piv_row, T* colbuf) {
   return true;
 }
 
+// In-place inverse of the complex m x m matrix (Sr + i Si) (row-major, leading dimension m) by
+// Gauss-Jordan elimination with partial pivoting on |a|; same structure as gauss_jordan.
+template <typename T>
+__device__ bool gauss_jordan_c(T* Sr, T* Si, int m, int* piv_row, T* cr, T* ci) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ int s_pivc;
+  __shared__ bool s_okc;
+  if (tid == 0) s_okc = true;
+  for (int p = 0; p < m; ++p) {
+    if (tid < 32) {
+      T best = -1; int bi = p;
+      for (int i = p + tid; i < m; i += 32) {
+        const T a = Sr[i * m + p] * Sr[i * m + p] + Si[i * m + p] * Si[i * m + p];
+        if (a > best) { best = a; bi = i; }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        T ob = __shfl_down_sync(0xffffffffu, best, off);
+        int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) { s_pivc = bi; piv_row[p] = bi; if (!(best > 0)) s_okc = false; }
+    }
+    __syncthreads();
+    if (!s_okc) return false;
+    const int r = s_pivc;
+    if (r != p)
+      for (int j = tid; j < m; j += nt) {
+        T t = Sr[p * m + j]; Sr[p * m + j] = Sr[r * m + j]; Sr[r * m + j] = t;
+        t = Si[p * m + j]; Si[p * m + j] = Si[r * m + j]; Si[r * m + j] = t;
+      }
+    __syncthreads();
+    const T pr = Sr[p * m + p], pi = Si[p * m + p];
+    const T den = (T)1 / (pr * pr + pi * pi);
+    const T qr = pr * den, qi = -pi * den;          // 1 / (pr + i pi)
+    __syncthreads();
+    for (int j = tid; j < m; j += nt) {
+      if (j == p) { Sr[p * m + j] = qr; Si[p * m + j] = qi; }
+      else {
+        const T ar = Sr[p * m + j], ai = Si[p * m + j];
+        Sr[p * m + j] = ar * qr - ai * qi; Si[p * m + j] = ar * qi + ai * qr;
+      }
+    }
+    for (int i = tid; i < m; i += nt) {
+      cr[i] = (i == p) ? (T)0 : Sr[i * m + p];
+      ci[i] = (i == p) ? (T)0 : Si[i * m + p];
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += nt) if (i != p) { Sr[i * m + p] = 0; Si[i * m + p] = 0; }
+    __syncthreads();
+    if (nt >= m) {
+      const int rs = nt / m;
+      if (tid < rs * m) {
+        const int j = tid % m, chunk = tid / m;
+        const T br = Sr[p * m + j], bim = Si[p * m + j];
+        for (int i = chunk; i < m; i += rs)
+          if (i != p) {
+            Sr[i * m + j] -= cr[i] * br - ci[i] * bim;
+            Si[i * m + j] -= cr[i] * bim + ci[i] * br;
+          }
+      }
+    } else {
+      for (int j = tid; j < m; j += nt) {
+        const T br = Sr[p * m + j], bim = Si[p * m + j];
+        for (int i = 0; i < m; ++i)
+          if (i != p) {
+            Sr[i * m + j] -= cr[i] * br - ci[i] * bim;
+            Si[i * m + j] -= cr[i] * bim + ci[i] * br;
+          }
+      }
+    }
+    __syncthreads();
+  }
+  for (int p = m - 1; p >= 0; --p) {
+    const int r = piv_row[p];
+    if (r != p)
+      for (int i = tid; i < m; i += nt) {
+        T t = Sr[i * m + p]; Sr[i * m + p] = Sr[i * m + r]; Sr[i * m + r] = t;
+        t = Si[i * m + p]; Si[i * m + p] = Si[i * m + r]; Si[i * m + r] = t;
+      }
+    __syncthreads();
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------------------- patch build
-// Patch-local ordering: velocity (a, c, i) -> a*MV + c*NL + i, then pressure (a, m) ->
-// KP1*MV + a*npc + m.
+// Spatial patch ordering: velocity (c, i) -> c*NL + i, then pressure mode m -> MV + m.  The
+// surrogate patch matrix of Eq. vanka0 is, time node by time node,
+//   S~ = [ K^tau (x) M + W (x) A ,  W (x) B^T ;  W (x) B , 0 ],   W = diag(w_a),
+// with the cell's assembled velocity mass M (per component), velocity block A (viscous,
+// convection at v*, Nitsche) and divergence block B.  With W^{-1} K^tau = Q diag(lam) Q^{-1}
+// it is similar to the block diagonal of T_lam = [lam M + A, B^T; B, 0]: one spatial inverse
+// per eigenvalue instead of one inverse of the whole space-time patch (Sec. 4.3).
 template <typename T, int D, int N>
-__global__ void k_patch(VankaArgs<T> V, Tab<T> tb, int64_t ncells) {
+__global__ void k_patch(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t ncells) {
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
-  const int kp1 = tb.k + 1, npc = tb.npc;
-  const int m = kp1 * (MV + npc);
+  const int npc = tb.npc, kp1 = tb.k + 1;
+  const int ms = MV + npc, st = inv_stride(ms);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* S = reinterpret_cast<T*>(smem_raw);           // [m][m]
-  T* Ap = S + m * m;                                // [MV][MV] assembled velocity block
+  T* Sr = reinterpret_cast<T*>(smem_raw);           // [ms][ms]
+  T* Si = Sr + ms * ms;                             // [ms][ms] imaginary part
+  T* Ap = Si + ms * ms;                             // [MV][MV] assembled velocity block
   T* Mp = Ap + MV * MV;                             // [NL][NL] assembled scalar mass
-  T* colbuf = Mp + NL * NL;                         // [m]
-  int* piv = reinterpret_cast<int*>(colbuf + m);    // [m]
+  T* cr = Mp + NL * NL;                             // [ms]
+  T* ci = cr + ms;                                  // [ms]
+  int* piv = reinterpret_cast<int*>(ci + ms);       // [ms]
   const int64_t cell = blockIdx.x;
   if (cell >= ncells) return;
   const LevelArgs<T>& L = V.L;
@@ -395,151 +489,218 @@ __global__ void k_patch(VankaArgs<T> V, Tab<T> tb, int64_t ncells) {
   }
   __syncthreads();
   const T* EB = V.EB + cell * (int64_t)npc * MV;
-  for (int ent = tid; ent < m * m; ent += nt) {
-    const int row = ent / m, col = ent % m;
-    T v = 0;
-    if (row < kp1 * MV && col < kp1 * MV) {
-      const int a = row / MV, rv = row % MV, b = col / MV, cv = col % MV;
-      if (rv / NL == cv / NL) v = tb.K[a][b] * Mp[(rv % NL) * NL + (cv % NL)];
-      if (a == b) v += tb.w[a] * Ap[rv * MV + cv];
-    } else if (row < kp1 * MV) {
-      const int a = row / MV, rv = row % MV, b = (col - kp1 * MV) / npc, pm = (col - kp1 * MV) % npc;
-      if (a == b) v = tb.w[a] * EB[pm * MV + rv];
-    } else if (col < kp1 * MV) {
-      const int a = (row - kp1 * MV) / npc, pm = (row - kp1 * MV) % npc, b = col / MV, cv = col % MV;
-      if (a == b) v = tb.w[a] * EB[pm * MV + cv];
+  const int64_t cbase = cell * (int64_t)kp1 * ms * st;
+  for (int e = 0; e < te.nblk; ++e) {
+    const bool cplx = te.cplx[e] != 0;
+    const T lr = te.lre[e], li = te.lim[e];
+    for (int ent = tid; ent < ms * ms; ent += nt) {
+      const int row = ent / ms, col = ent % ms;
+      T vr = 0, vi = 0;
+      if (row < MV && col < MV) {
+        vr = Ap[row * MV + col];
+        if (row / NL == col / NL) {
+          const T mm = Mp[(row % NL) * NL + (col % NL)];
+          vr += lr * mm; vi = li * mm;
+        }
+      } else if (row < MV) {
+        vr = EB[(col - MV) * MV + row];
+      } else if (col < MV) {
+        vr = EB[(row - MV) * MV + col];
+      }
+      Sr[ent] = vr;
+      Si[ent] = vi;
     }
-    S[ent] = v;
-  }
-  __syncthreads();
-  bool ok = gauss_jordan<T>(S, m, m, piv, colbuf);
-  if (!ok) { if (tid == 0) *V.status = 1; return; }
-  if (V.invh) {
-    T mx = 0;
-    for (int ent = tid; ent < m * m; ent += nt) mx = fmax(mx, fabs(S[ent]));
-    mx = block_absmax<T>(mx);
-    // the scale is held in FP32: divide by exactly the value the apply multiplies by
-    const float sc = mx > 0 ? (float)mx : 1.f;
-    const T isc = (T)1 / (T)sc;
-    if (tid == 0) V.scale[cell] = sc;
-    const int ms = inv_stride(m);
-    __half* inv = V.invh + cell * (int64_t)m * ms;
-    for (int ent = tid; ent < m * ms; ent += nt) {
-      const int j = ent / ms, i = ent % ms;
-      inv[ent] = __float2half_rn(i < m ? (float)(S[i * m + j] * isc) : 0.f);
+    __syncthreads();
+    const bool ok = cplx ? gauss_jordan_c<T>(Sr, Si, ms, piv, cr, ci) : gauss_jordan<T>(Sr, ms, ms, piv, cr);
+    if (!ok) { if (tid == 0) *V.status = 1; return; }
+    const int w = cplx ? 2 : 1;                                  // reals per stored entry
+    const int64_t bbase = cbase + (int64_t)te.off[e] * ms * st;  // in reals
+    if (V.invh) {
+      T mx = 0;
+      for (int ent = tid; ent < ms * ms; ent += nt) mx = fmax(mx, fmax(fabs(Sr[ent]), cplx ? fabs(Si[ent]) : (T)0));
+      mx = block_absmax<T>(mx);
+      // the scale is held in FP32: divide by exactly the value the apply multiplies by
+      const float sc = mx > 0 ? (float)mx : 1.f;
+      const T isc = (T)1 / (T)sc;
+      if (tid == 0) V.scale[cell * te.nblk + e] = sc;
+      __half* inv = V.invh + bbase;
+      for (int ent = tid; ent < ms * st; ent += nt) {
+        const int j = ent / st, i = ent % st;
+        const bool in = i < ms;
+        inv[(int64_t)w * ent] = __float2half_rn(in ? (float)(Sr[i * ms + j] * isc) : 0.f);
+        if (cplx) inv[(int64_t)w * ent + 1] = __float2half_rn(in ? (float)(Si[i * ms + j] * isc) : 0.f);
+      }
+    } else {
+      T* inv = V.inv + bbase;
+      for (int ent = tid; ent < ms * st; ent += nt) {
+        const int j = ent / st, i = ent % st;     // column-major: inv[j][i] = T^{-1}[i][j]
+        const bool in = i < ms;                   // rows ms..st-1 pad the column
+        inv[(int64_t)w * ent] = in ? Sr[i * ms + j] : (T)0;
+        if (cplx) inv[(int64_t)w * ent + 1] = in ? Si[i * ms + j] : (T)0;
+      }
     }
-    return;
-  }
-  const int ms = inv_stride(m);
-  T* inv = V.inv + cell * (int64_t)m * ms;
-  for (int ent = tid; ent < m * ms; ent += nt) {
-    const int j = ent / ms, i = ent % ms;        // column-major store: inv[j][i] = S^{-1}[i][j]
-    inv[ent] = i < m ? S[i * m + j] : (T)0;      // rows m..ms-1 pad the column to 16 bytes
+    __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------- sweep
-// d[patch] += omega * S~^{-1} res[patch] for the cells of one colour.
-//
-// The inverse of a patch is stored column-major with a padded column stride ms = inv_stride(m)
-// in SI = T, or in FP16 scaled per cell by scale[cell].  TPC threads (a multiple of 32) serve
-// one cell and a block holds blockDim / TPC cells.  A thread owns RR consecutive rows (1 for T,
-// 2 for FP16: one 4-byte load per column either way, so FP16 halves the bytes at the same
-// instruction count) and keeps kApplyUnroll column loads in flight before their FMAs; the
-// threads of a cell read each column as one contiguous segment.  Accumulation in T.
-constexpr int kApplyUnroll = 8;
+// d[patch] += W~ S~^{-1} res[patch] for the cells of one colour (W~ = omega on velocity,
+// omega_p on pressure DoFs), through the time-diagonalised inverse (k_patch):
+//   rt_e = sum_a F[e][a] res_a  (per spatial patch DoF),  yhat_e = T_e^{-1} rt_e,
+//   y_a = sum_e Re(G[a][e] yhat_e).
+// One block per cell.  Its inverse ((k+1) m_s x stride reals, contiguous) is staged into shared
+// memory by one bulk asynchronous copy (cp.async.bulk, completion on an mbarrier) issued before
+// the residual gather, so the whole blob is in flight while the block gathers and transforms
+// the residual; thread i then owns spatial row i of every block.  Accumulation in T.
 
-template <typename SI> struct InvRows;
-template <> struct InvRows<float> {
-  static constexpr int RR = 1;
-  using raw = float;
-  __device__ static raw ld(const float* p) { return __ldg(p); }
-  __device__ static void get(raw v, float* o) { o[0] = v; }
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(bar), "r"(phase) : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `phase` of the mbarrier (each try_wait suspends for a bounded time).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase, int limit) {
+  for (int it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+constexpr int kBulkChunk = 32768;        // bytes per bulk copy instruction
+constexpr int kWaitLimit = 1 << 20;      // try_wait rounds before the wait is declared failed
+
+template <typename SI> struct InvLd;
+template <> struct InvLd<float> {
+  __device__ static float re(const float* p) { return *p; }
+  __device__ static float2 cx(const float* p) { return *reinterpret_cast<const float2*>(p); }
 };
-template <> struct InvRows<double> {
-  static constexpr int RR = 1;
-  using raw = double;
-  __device__ static raw ld(const double* p) { return __ldg(p); }
-  __device__ static void get(raw v, double* o) { o[0] = v; }
+template <> struct InvLd<double> {
+  __device__ static double re(const double* p) { return *p; }
+  __device__ static double2 cx(const double* p) { return *reinterpret_cast<const double2*>(p); }
 };
-template <> struct InvRows<__half> {
-  static constexpr int RR = 2;
-  using raw = __half2;
-  __device__ static raw ld(const __half* p) { return __ldg(reinterpret_cast<const __half2*>(p)); }
-  __device__ static void get(raw v, float* o) { const float2 f = __half22float2(v); o[0] = f.x; o[1] = f.y; }
+template <> struct InvLd<__half> {
+  __device__ static float re(const __half* p) { return __half2float(*p); }
+  __device__ static float2 cx(const __half* p) { return __half22float2(*reinterpret_cast<const __half2*>(p)); }
 };
-template <typename SI> struct InvVal { using type = SI; };
-template <> struct InvVal<__half> { using type = float; };
+
+// Dynamic shared memory of k_vanka_apply: [blob | rt (kp1 x mr T) | gb (ms int64) | mbarrier].
+__host__ __device__ inline size_t apply_blob_bytes(int kp1, int ms, size_t si) {
+  return ((size_t)kp1 * ms * inv_stride(ms) * si + 127) & ~(size_t)127;
+}
+__host__ __device__ inline size_t apply_smem_bytes(int kp1, int ms, size_t si, size_t t) {
+  const int mr = (ms + 1) & ~1;
+  return apply_blob_bytes(kp1, ms, si) + (((size_t)kp1 * mr * t + 7) & ~(size_t)7) + (size_t)ms * 8 + 16;
+}
 
 template <typename T, typename SI, int D, int N>
 __global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const float* __restrict__ scale,
                               const T* __restrict__ res, T* __restrict__ d, T omega, T omega_p, int kp1, int npc,
-                              int tpc, ColorInfo ci) {
+                              TEig<T> te, ColorInfo ci, int* __restrict__ wstat) {
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
-  constexpr int RR = InvRows<SI>::RR;
-  using V = typename InvVal<SI>::type;
-  using W = typename InvRows<SI>::raw;
-  const int m = kp1 * (MV + npc), ms = inv_stride(m), mr = (m + 1) & ~1;
-  const int cpb = blockDim.x / tpc;
+  const int ms = MV + npc, st = inv_stride(ms), mr = (ms + 1) & ~1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int slot = threadIdx.x / tpc, tid = threadIdx.x % tpc;
-  T* r = reinterpret_cast<T*>(smem_raw) + slot * mr;
-  int64_t* gidx = reinterpret_cast<int64_t*>(reinterpret_cast<T*>(smem_raw) + cpb * mr) + slot * m;
-  const int cidx = blockIdx.x * cpb + slot;
-  const bool active = cidx < ci.count;
-  int64_t cell = 0;
-  if (active) {
-    int cc[3] = {0, 0, 0};
-    decode_color_cell<D>(ci, cidx, cc);
-    int64_t s = 1;
-    for (int l = 0; l < D; ++l) { cell += (int64_t)cc[l] * s; s *= L.n; }
-    for (int l = tid; l < m; l += tpc) {
-      int64_t g;
-      if (l < kp1 * MV) {
-        const int a = l / MV, rv = l % MV, c = rv / NL, i = rv % NL;
-        g = (int64_t)a * L.Nv + c * L.nnodes + global_node<D>(L.N1, cc, N - 1, i, N);
-      } else {
-        const int a = (l - kp1 * MV) / npc, pm = (l - kp1 * MV) % npc;
-        g = (int64_t)kp1 * L.Nv + (int64_t)a * L.Np + cell * npc + pm;
+  const size_t blob = apply_blob_bytes(kp1, ms, sizeof(SI));
+  SI* sinv = reinterpret_cast<SI*>(smem_raw);
+  T* rt = reinterpret_cast<T*>(smem_raw + blob);                                      // [kp1 units][mr]
+  int64_t* gb = reinterpret_cast<int64_t*>(smem_raw + blob + (((size_t)kp1 * mr * sizeof(T) + 7) & ~(size_t)7));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(gb + ms);
+  const int cidx = blockIdx.x;
+  if (cidx >= ci.count) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int cc[3] = {0, 0, 0};
+  decode_color_cell<D>(ci, cidx, cc);
+  int64_t cell = 0, s = 1;
+  for (int l = 0; l < D; ++l) { cell += (int64_t)cc[l] * s; s *= L.n; }
+  // stage the cell's inverse: one thread arms the barrier and issues the bulk copies
+  const uint32_t b = smem_addr(bar);
+  const uint32_t bytes = (uint32_t)((size_t)kp1 * ms * st * sizeof(SI));
+  if (tid == 0) {
+    mbar_init(b, 1);
+    mbar_expect_tx(b, bytes);
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(inv + cell * (int64_t)kp1 * ms * st);
+    for (uint32_t o = 0; o < bytes; o += kBulkChunk) {
+      const uint32_t n = bytes - o < (uint32_t)kBulkChunk ? bytes - o : (uint32_t)kBulkChunk;
+      bulk_g2s(smem_addr(smem_raw + o), src + o, n, b);
+    }
+  }
+  // meanwhile: gather the residual on the patch and transform it to the time eigenbasis
+  for (int l = tid; l < ms; l += nt) {
+    int64_t g, sa;
+    if (l < MV) {
+      const int c = l / NL, i = l % NL;
+      g = c * L.nnodes + global_node<D>(L.N1, cc, N - 1, i, N);
+      sa = L.Nv;
+    } else {
+      g = (int64_t)kp1 * L.Nv + cell * npc + (l - MV);
+      sa = L.Np;
+    }
+    gb[l] = g;
+    T ra[MAXKP1];
+#pragma unroll
+    for (int a = 0; a < MAXKP1; ++a) ra[a] = a < kp1 ? res[g + a * sa] : (T)0;
+    for (int e = 0; e < te.nblk; ++e) {
+      T fr = 0, fi = 0;
+#pragma unroll
+      for (int a = 0; a < MAXKP1; ++a) { fr += te.Fre[e][a] * ra[a]; fi += te.Fim[e][a] * ra[a]; }
+      rt[te.off[e] * mr + l] = fr;
+      if (te.cplx[e]) rt[(te.off[e] + 1) * mr + l] = fi;
+    }
+  }
+  __syncthreads();                                   // barrier initialised, rt and gb complete
+  if (!mbar_wait_bounded(b, 0, kWaitLimit)) {
+    // the copy did not complete in time: report, give it a second bounded wait (it writes this
+    // block's shared memory) and leave d unchanged for this cell
+    if (tid == 0) atomicExch(wstat, 1);
+    mbar_wait_bounded(b, 0, kWaitLimit);
+    return;
+  }
+  const int i = tid;
+  if (i >= ms) return;
+  T yr[MAXKP1], yi[MAXKP1];
+#pragma unroll
+  for (int e = 0; e < MAXKP1; ++e) { yr[e] = 0; yi[e] = 0; }
+  for (int e = 0; e < te.nblk; ++e) {
+    const SI* blk = sinv + (int64_t)te.off[e] * ms * st;
+    const T* r0 = rt + te.off[e] * mr;
+    T ar = 0, ai = 0;
+    if (!te.cplx[e]) {
+      for (int j = 0; j < ms; ++j) ar += (T)InvLd<SI>::re(blk + j * st + i) * r0[j];
+    } else {
+      const T* r1 = r0 + mr;
+      for (int j = 0; j < ms; ++j) {
+        const auto v = InvLd<SI>::cx(blk + 2 * (j * st + i));
+        const T vr = (T)v.x, vi = (T)v.y, xr = r0[j], xi = r1[j];
+        ar += vr * xr - vi * xi;
+        ai += vr * xi + vi * xr;
       }
-      gidx[l] = g;
-      r[l] = res[g];
     }
+    const T sc = scale ? (T)scale[cell * te.nblk + e] : (T)1;
+#pragma unroll
+    for (int q = 0; q < MAXKP1; ++q)
+      if (q == e) { yr[q] = sc * ar; yi[q] = sc * ai; }
   }
-  __syncthreads();
-  const int i0 = tid * RR;
-  if (!active || i0 >= m) return;
-  const SI* col = inv + cell * (int64_t)m * ms + i0;
-  T acc[RR];
+  const int64_t g = gb[i];
+  const int64_t sa = i < MV ? L.Nv : L.Np;
+  const T wgt = i < MV ? omega : omega_p;
+  for (int a = 0; a < kp1; ++a) {
+    T y = 0;
 #pragma unroll
-  for (int t = 0; t < RR; ++t) acc[t] = 0;
-  int j = 0;
-  for (; j + kApplyUnroll <= m; j += kApplyUnroll) {
-    W w[kApplyUnroll];
-#pragma unroll
-    for (int u = 0; u < kApplyUnroll; ++u) w[u] = InvRows<SI>::ld(col + (int64_t)(j + u) * ms);
-#pragma unroll
-    for (int u = 0; u < kApplyUnroll; ++u) {
-      V v[RR];
-      InvRows<SI>::get(w[u], v);
-      const T ru = r[j + u];
-#pragma unroll
-      for (int t = 0; t < RR; ++t) acc[t] += (T)v[t] * ru;
-    }
-  }
-  for (; j < m; ++j) {
-    V v[RR];
-    InvRows<SI>::get(InvRows<SI>::ld(col + (int64_t)j * ms), v);
-    const T rj = r[j];
-#pragma unroll
-    for (int t = 0; t < RR; ++t) acc[t] += (T)v[t] * rj;
-  }
-  const T sc = scale ? (T)scale[cell] : (T)1;
-#pragma unroll
-  for (int t = 0; t < RR; ++t) {
-    const int i = i0 + t;
-    if (i < m) d[gidx[i]] += (i < kp1 * MV ? omega : omega_p) * sc * acc[t];
+    for (int e = 0; e < MAXKP1; ++e)
+      if (e < te.nblk) y += te.Gre[a][e] * yr[e] - te.Gim[a][e] * yi[e];
+    d[g + a * sa] += wgt * y;
   }
 }
 

@@ -81,6 +81,7 @@ def load():
         "stmg_transfer": (I, [P, I, I, V, V]),
         "stmg_level_state": (I, [P, I, V]),
         "stmg_set_timing": (I, [P, I]),
+        "stmg_set_timing_classes": (I, [P, ctypes.c_uint]),
         "stmg_slab_solve": (I, [P, D, V, V, ctypes.POINTER(Stats)]),
         "stmg_kernel_profile": (I, [P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                     ctypes.POINTER(ctypes.c_double)]),
@@ -240,7 +241,11 @@ class Solver:
         self._check(self.lib.stmg_level_state(self.h, level, _ptr(out, self.pdtype, self.levels[level]["Nst"], "out")),
                     "level_state")
 
-    def set_timing(self, on=True):
+    def set_timing(self, on=True, classes=None):
+        """Phase and kernel-class timers; `classes`: iterable of kernel-class indices to time
+        (None: all)."""
+        mask = 0xFFFFFFFF if classes is None else sum(1 << c for c in classes)
+        self._check(self.lib.stmg_set_timing_classes(self.h, mask), "set_timing_classes")
         self._check(self.lib.stmg_set_timing(self.h, int(on)), "set_timing")
 
     def set_physics(self, nu, tau, problem):
