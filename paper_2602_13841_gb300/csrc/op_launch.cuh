@@ -61,8 +61,10 @@ static cudaError_t launch_dn(const Level& lv, const Problem& pb, double t0, cons
     const ColorInfo& ci = lv.colors[c];
     if (ci.count > 0) {
       if constexpr (D == 2) {
+        // one group of Q lanes per (cell, time node)
         constexpr int cpw = 32 / Q, per_block = 8 * cpw;
-        dim3 grid((ci.count + per_block - 1) / per_block, batch);
+        const int64_t groups = (int64_t)ci.count * kp1;
+        dim3 grid((unsigned)((groups + per_block - 1) / per_block), batch);
         k_volume2d<T, N, MODE><<<grid, 256, 0, stream>>>(A, tb, ci);
       } else {
         dim3 grid((ci.count + cpb - 1) / cpb, batch);

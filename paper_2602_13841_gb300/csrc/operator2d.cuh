@@ -192,46 +192,62 @@ __device__ __forceinline__ void face2d(const OpArgs<T>& A, const Tab<T>& tb, int
 }
 
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(256) k_volume2d(OpArgs<T> A, Tab<T> tb, ColorInfo ci) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_volume2d(OpArgs<T> A, Tab<T> tb, ColorInfo ci) {
   constexpr int Q = N * N;
-  constexpr int CPW = 32 / Q;                       // cells per warp
+  constexpr int CPW = 32 / Q;                       // (cell, time node) groups per warp
   constexpr bool RES = (MODE == MR);
   constexpr bool MASS = (MODE == MM);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int slot = lane / Q;                        // cell slot inside the warp
+  const int slot = lane / Q;                        // group slot inside the warp
   const int t = lane - slot * Q;                    // quadrature point / local node
   const int tx = t % N, ty = t / N;
-  const int cb = slot * Q;                          // first lane of this cell
-  const int cidx = (blockIdx.x * (blockDim.x >> 5) + warp) * CPW + slot;
+  const int cb = slot * Q;                          // first lane of this group
+  const int kp1 = tb.k + 1, npc = tb.npc;
+  // 1D tables in shared memory: the passes index them by the lane's row (tx or ty), which
+  // would serialise constant-bank reads of the kernel parameters
+  __shared__ T sB[MAXN][MAXN], sDc[MAXN][MAXN], sP1[MAXN][4];
+  for (int e = threadIdx.x; e < MAXN * MAXN; e += blockDim.x) {
+    sB[e / MAXN][e % MAXN] = tb.B[e / MAXN][e % MAXN];
+    sDc[e / MAXN][e % MAXN] = tb.Dc[e / MAXN][e % MAXN];
+  }
+  for (int e = threadIdx.x; e < MAXN * 4; e += blockDim.x) sP1[e / 4][e % 4] = tb.P1[e / 4][e % 4];
+  __syncthreads();
+  // one group of Q lanes per (cell, time node a): the time nodes of a cell couple only through
+  // K^tau (and C^tau v_{n-1}), which is applied to the nodal values before the interpolation
+  const int grp = (blockIdx.x * (blockDim.x >> 5) + warp) * CPW + slot;
+  const int cidx = grp / kp1, a = grp - cidx * kp1;
   const bool on = (slot < CPW) && (cidx < ci.count);
   A.x += blockIdx.y * A.xs;
   A.y += blockIdx.y * A.ys;
   const LevelArgs<T>& L = A.L;
-  const int kp1 = tb.k + 1, npc = tb.npc;
   int cc[3] = {0, 0, 0};
   if (on) decode_color_cell<2>(ci, cidx, cc);
   const int64_t gnode = on ? (int64_t)(cc[0] * (N - 1) + tx) + (int64_t)L.N1 * (cc[1] * (N - 1) + ty) : 0;
   const int64_t cell = (int64_t)cc[0] + (int64_t)L.n * cc[1];
   const int64_t poff = (int64_t)kp1 * L.Nv;
+  const T wa = tb.w[a];
 
-  // ---- loads (node values; lane t holds local node t)
-  T dv[MAXKP1][2], st[MAXKP1][2], pm[MAXKP1], vp[2] = {0, 0};
+  // ---- loads (node values; lane t holds local node t): the increment and the state at time
+  // node a, and the time-mixed nodal vector u = sum_b K[a][b] x_b (- C[a] v_prev) or w_a x_a
+  T dva[2] = {0, 0}, va[2] = {0, 0}, u[2] = {0, 0}, pma = 0;
 #pragma unroll
-  for (int b = 0; b < MAXKP1; ++b) {
-    pm[b] = 0;
+  for (int c = 0; c < 2; ++c) {
+    if (!on) continue;
+    const int64_t gi = c * L.nnodes + gnode;
+    dva[c] = A.x[(int64_t)a * L.Nv + gi];
+    va[c] = (MODE == MJ) ? A.state[(int64_t)a * L.Nv + gi] : dva[c];
+    T acc = 0;
+    if (MASS) {
+      acc = wa * dva[c];
+    } else {
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      dv[b][c] = 0; st[b][c] = 0;
-      if (on && b < kp1) {
-        const int64_t gi = (int64_t)b * L.Nv + c * L.nnodes + gnode;
-        dv[b][c] = A.x[gi];
-        if (MODE == MJ) st[b][c] = A.state[gi];
-      }
+      for (int b = 0; b < MAXKP1; ++b)
+        if (b < kp1) acc += tb.K[a][b] * (b == a ? dva[c] : A.x[(int64_t)b * L.Nv + gi]);
+      if (RES) acc -= tb.C[a] * A.vprev[gi];
     }
-    if (on && b < kp1 && t < npc) pm[b] = A.x[poff + (int64_t)b * L.Np + cell * npc + t];
+    u[c] = acc;
   }
-  if (RES && on)
-    for (int c = 0; c < 2; ++c) vp[c] = A.vprev[c * L.nnodes + gnode];
+  if (on && t < npc) pma = A.x[poff + (int64_t)a * L.Np + cell * npc + t];
   // corners and geometry at quadrature point t
   T corner[4][3];
   {
@@ -249,132 +265,102 @@ __global__ void __launch_bounds__(256) k_volume2d(OpArgs<T> A, Tab<T> tb, ColorI
     JxW = invert<T, 2>(J, G) * tb.qw[tx] * tb.qw[ty];
   }
   // ---- node values -> quadrature values (two shuffle passes per array)
+  T dq[2], sq[2], uq[2];
 #pragma unroll
-  for (int b = 0; b < MAXKP1; ++b)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      if (b < kp1) {
-        T v = shfl_x<T, N>(dv[b][c], tb.B, tx, cb + ty * N, false);
-        dv[b][c] = shfl_y<T, N>(v, tb.B, ty, cb + tx, false);
-        if (MODE == MJ) {
-          v = shfl_x<T, N>(st[b][c], tb.B, tx, cb + ty * N, false);
-          st[b][c] = shfl_y<T, N>(v, tb.B, ty, cb + tx, false);
-        }
-      }
+  for (int c = 0; c < 2; ++c) {
+    T v = shfl_x<T, N>(dva[c], sB, tx, cb + ty * N, false);
+    dq[c] = shfl_y<T, N>(v, sB, ty, cb + tx, false);
+    if (MODE == MJ) {
+      v = shfl_x<T, N>(va[c], sB, tx, cb + ty * N, false);
+      sq[c] = shfl_y<T, N>(v, sB, ty, cb + tx, false);
+    } else {
+      sq[c] = dq[c];
     }
-  if (RES)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      T v = shfl_x<T, N>(vp[c], tb.B, tx, cb + ty * N, false);
-      vp[c] = shfl_y<T, N>(v, tb.B, ty, cb + tx, false);
-    }
+    v = shfl_x<T, N>(u[c], sB, tx, cb + ty * N, false);
+    uq[c] = shfl_y<T, N>(v, sB, ty, cb + tx, false);
+  }
   // cell volume |K| (for h_{Gamma_D} of boundary faces)
   T vol = 0;
 #pragma unroll
   for (int q = 0; q < Q; ++q) vol += __shfl_sync(0xffffffffu, JxW, cb + q);
-  // pressure basis at this quadrature point
-  T psi[MAXNP2D];
+  // pressure at this quadrature point
+  T pq = 0;
 #pragma unroll
-  for (int m = 0; m < MAXNP2D; ++m) psi[m] = (m < npc) ? tb.P1[tx][tb.modes[m][0]] * tb.P1[ty][tb.modes[m][1]] : (T)0;
-
-  for (int a = 0; a < kp1; ++a) {
-    // select time node a (registers are indexed statically)
-    T dva[2], va[2], pma = 0;
-#pragma unroll
-    for (int b = 0; b < MAXKP1; ++b)
-      if (b == a) {
-        dva[0] = dv[b][0]; dva[1] = dv[b][1]; va[0] = st[b][0]; va[1] = st[b][1]; pma = pm[b];
-      }
-    if (MODE != MJ) { va[0] = dva[0]; va[1] = dva[1]; }
-    // reference gradients by the collocation derivative
-    T gref[2][2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      gref[c][0] = shfl_x<T, N>(dva[c], tb.Dc, tx, cb + ty * N, false);
-      gref[c][1] = shfl_y<T, N>(dva[c], tb.Dc, ty, cb + tx, false);
-    }
-    T pq = 0;
-#pragma unroll
-    for (int m = 0; m < MAXNP2D; ++m) {
-      if (m < npc) pq += psi[m] * __shfl_sync(0xffffffffu, pma, cb + m);
-    }
-    T gp[2][2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-      for (int l = 0; l < 2; ++l) gp[c][l] = G[0][l] * gref[c][0] + G[1][l] * gref[c][1];
-    const T wa = tb.w[a];
-    T Fh[2][2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      T F[2];
-#pragma unroll
-      for (int l = 0; l < 2; ++l) {
-        T conv = RES ? va[c] * va[l] : dva[c] * va[l] + va[c] * dva[l];
-        F[l] = MASS ? (T)0 : L.nu * gp[c][l] - conv - ((c == l) ? pq : (T)0);
-      }
-#pragma unroll
-      for (int m = 0; m < 2; ++m) Fh[c][m] = wa * JxW * (G[m][0] * F[0] + G[m][1] * F[1]);
-    }
-    T fq[2] = {0, 0};
-    if (RES && on) {
-      double xd[3] = {(double)xq[0], (double)xq[1], 0.0}, fd[3];
-      const double ta = (double)L.t0 + 0.5 * (double)L.tau * ((double)tb.that[a] + 1.0);
-      problem_f<2>(L.problem, xd, ta, (double)L.nu, fd);
-      fq[0] = (T)fd[0]; fq[1] = (T)fd[1];
-    }
-    T z[2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      T acc = 0;
-      if (MASS) {
-        acc = wa * dva[c];
-      } else {
-#pragma unroll
-        for (int b = 0; b < MAXKP1; ++b)
-          if (b < kp1) acc += tb.K[a][b] * dv[b][c];
-      }
-      if (RES) acc -= tb.C[a] * vp[c] + wa * fq[c];
-      z[c] = JxW * acc;
-    }
-    const T sp = MASS ? wa * JxW * pq : -wa * JxW * (gp[0][0] + gp[1][1]);
-    // gradient test functions at the Gauss points (transposed collocation derivative)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      z[c] += shfl_x<T, N>(Fh[c][0], tb.Dc, tx, cb + ty * N, true);
-      z[c] += shfl_y<T, N>(Fh[c][1], tb.Dc, ty, cb + tx, true);
-    }
-    // quadrature -> nodes (transposed B passes)
-    T vout[2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      T v = shfl_x<T, N>(z[c], tb.B, tx, cb + ty * N, true);
-      vout[c] = shfl_y<T, N>(v, tb.B, ty, cb + tx, true);
-    }
-    // pressure test functions: lane cb + m accumulates sum_t psi_m(t) sp(t)
-    T pacc = 0;
-    const int mo = t < npc ? t : 0;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      T s = __shfl_sync(0xffffffffu, sp, cb + q);
-      pacc += tb.P1[q % N][tb.modes[mo][0]] * tb.P1[q / N][tb.modes[mo][1]] * s;
-    }
-    // boundary faces (Nitsche, boundary convection) of boundary cells
-    if (MODE != MM) {
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const int axis = f >> 1, side = f & 1;
-        const bool has = on && (side == 0 ? cc[axis] == 0 : cc[axis] == L.n - 1);
-        if (__any_sync(0xffffffffu, has))
-          face2d<T, N, MODE>(A, tb, a, axis, side, has, corner, cc, gnode, cell, tx, ty, t, cb, vol, vout, pacc);
-      }
-    }
-    if (on) {
-#pragma unroll
-      for (int c = 0; c < 2; ++c) A.y[(int64_t)a * L.Nv + c * L.nnodes + gnode] += vout[c];
-    }
-    if (on && t < npc) A.y[poff + (int64_t)a * L.Np + cell * npc + t] += pacc;
+  for (int m = 0; m < MAXNP2D; ++m) {
+    const T pm = __shfl_sync(0xffffffffu, pma, cb + (m < Q ? m : 0));
+    if (m < npc) pq += sP1[tx][tb.modes[m][0]] * sP1[ty][tb.modes[m][1]] * pm;
   }
+  // reference gradients by the collocation derivative of the Gauss-point values
+  T gref[2][2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    gref[c][0] = shfl_x<T, N>(dq[c], sDc, tx, cb + ty * N, false);
+    gref[c][1] = shfl_y<T, N>(dq[c], sDc, ty, cb + tx, false);
+  }
+  T gp[2][2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int l = 0; l < 2; ++l) gp[c][l] = G[0][l] * gref[c][0] + G[1][l] * gref[c][1];
+  T Fh[2][2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    T F[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      T conv = RES ? sq[c] * sq[l] : dq[c] * sq[l] + sq[c] * dq[l];
+      F[l] = MASS ? (T)0 : L.nu * gp[c][l] - conv - ((c == l) ? pq : (T)0);
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) Fh[c][m] = wa * JxW * (G[m][0] * F[0] + G[m][1] * F[1]);
+  }
+  T fq[2] = {0, 0};
+  if (RES && on) {
+    double xd[3] = {(double)xq[0], (double)xq[1], 0.0}, fd[3];
+    const double ta = (double)L.t0 + 0.5 * (double)L.tau * ((double)tb.that[a] + 1.0);
+    problem_f<2>(L.problem, xd, ta, (double)L.nu, fd);
+    fq[0] = (T)fd[0]; fq[1] = (T)fd[1];
+  }
+  T z[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) z[c] = JxW * (uq[c] - (RES ? wa * fq[c] : (T)0));
+  const T sp = MASS ? wa * JxW * pq : -wa * JxW * (gp[0][0] + gp[1][1]);
+  // gradient test functions at the Gauss points (transposed collocation derivative)
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    z[c] += shfl_x<T, N>(Fh[c][0], sDc, tx, cb + ty * N, true);
+    z[c] += shfl_y<T, N>(Fh[c][1], sDc, ty, cb + tx, true);
+  }
+  // quadrature -> nodes (transposed B passes)
+  T vout[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    T v = shfl_x<T, N>(z[c], sB, tx, cb + ty * N, true);
+    vout[c] = shfl_y<T, N>(v, sB, ty, cb + tx, true);
+  }
+  // pressure test functions: lane cb + m accumulates sum_t psi_m(t) sp(t)
+  T pacc = 0;
+  const int mo = t < npc ? t : 0;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    T sv = __shfl_sync(0xffffffffu, sp, cb + q);
+    pacc += sP1[q % N][tb.modes[mo][0]] * sP1[q / N][tb.modes[mo][1]] * sv;
+  }
+  // boundary faces (Nitsche, boundary convection) of boundary cells
+  if (MODE != MM) {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const int axis = f >> 1, side = f & 1;
+      const bool has = on && (side == 0 ? cc[axis] == 0 : cc[axis] == L.n - 1);
+      if (__any_sync(0xffffffffu, has))
+        face2d<T, N, MODE>(A, tb, a, axis, side, has, corner, cc, gnode, cell, tx, ty, t, cb, vol, vout, pacc);
+    }
+  }
+  if (on) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) A.y[(int64_t)a * L.Nv + c * L.nnodes + gnode] += vout[c];
+  }
+  if (on && t < npc) A.y[poff + (int64_t)a * L.Np + cell * npc + t] += pacc;
 }
 
 }  // namespace stmg
