@@ -154,3 +154,41 @@ def test_full_size_apply_and_residual_sampled_cells():
         got = R[B.slab_map[B.rows]]
         want = Rb[B.rows]
         assert np.abs(got - want).max() < 1e-12 * np.abs(want).max(), cell
+
+
+@pytest.mark.parametrize("d,n,r,k,amp,nu,tau,pname", [
+    (3, 64, 2, 1, 0.0, 1.0 / 1600, 0.02, "TG3D"),    # 3D 64^3 Cartesian, Q3/P2, DG(1), Re 1600
+    (3, 128, 1, 2, 0.1, 1.0 / 400, 0.01, "MMS3D"),   # 3D 128^3 mapped, Q2/P1, DG(2), Re 400
+])
+def test_full_size_3d_apply_and_residual_sampled_cells(d, n, r, k, amp, nu, tau, pname):
+    """The 3D workloads at full size: Jacobian apply and residual on the whole mesh, checked on
+    sampled cells (a corner, a boundary-face cell, an interior cell) against the oracle on the
+    5^3 block around each."""
+    import torch
+    from paper_2602_13841_gb300 import stmg
+    S, verts = _solver(d, n, r, k, amp, seed=1234, nu=nu, tau=tau, problem=pname)
+    L = S.levels[0]
+    U = inputs.uniform(L["Nst"], 52)
+    x = inputs.uniform(L["Nst"], 53)
+    Vp = inputs.uniform(L["Nv"], 54)
+    y = torch.empty(L["Nst"], dtype=torch.float64, device="cuda")
+    S.apply(_t(U), _t(x), y, 0, stmg.STMG_FP64)
+    R = torch.empty(L["Nst"], dtype=torch.float64, device="cuda")
+    S.residual(0.3, _t(U), _t(Vp), R)
+    torch.cuda.synchronize()
+    y, R = y.cpu().numpy(), R.cpu().numpy()
+    rng = np.random.default_rng(1)
+    cells = [(0, 0, 0), (n // 2, 0, n // 3), tuple(int(c) for c in rng.integers(1, n - 1, 3))]
+    if r >= 2:                      # the oracle's Q3 block takes ~20 s per assembly: two cells
+        cells = [cells[0], cells[2]]
+    prob = problems.make(pname, nu)
+    td = TimeData(k, tau)
+    for cell in cells:
+        B = Block(d, n, r, k, verts, list(cell))
+        Ub, xb = U[B.slab_map], x[B.slab_map]
+        yb = forms.jacobian(B.space, td, Ub, nu) @ xb
+        got, want = y[B.slab_map[B.rows]], yb[B.rows]
+        assert np.abs(got - want).max() < 1e-12 * np.abs(want).max(), cell
+        Rb = forms.residual(B.space, td, Ub, Vp[B.vel_map], prob, 0.3)
+        got, want = R[B.slab_map[B.rows]], Rb[B.rows]
+        assert np.abs(got - want).max() < 1e-12 * np.abs(want).max(), cell
