@@ -104,7 +104,7 @@ def _cpu_cores():
         return os.cpu_count() or 1
 
 
-def oracle_sample(n=16, slabs=1):
+def oracle_sample(n=16, slabs=1, smooth=SMOOTH["nu1"]):
     """FP64 CPU oracle slab solves on a bounded sample: the workload's (d, r, k, dt, Re, mesh
     recipe) on an n x n mesh.  Returns (DoF/s, seconds, N_st, description)."""
     from oracle import forms, krylov, problems
@@ -112,7 +112,8 @@ def oracle_sample(n=16, slabs=1):
     w = WORKLOAD
     prob = problems.make(w["problem"], w["nu"])
     verts = inputs.vertices(w["d"], n, w["amp"], w["seed"])
-    S = krylov.SlabSolver(w["d"], n, w["r"], w["k"], verts, w["tau"], prob, rtol=1e-10, atol=ATOL, **SMOOTH)
+    S = krylov.SlabSolver(w["d"], n, w["r"], w["k"], verts, w["tau"], prob, rtol=1e-10, atol=ATOL,
+                          **dict(SMOOTH, nu1=smooth, nu2=smooth))
     L = S.L
     Vprev = forms.interpolate_velocity(L.space, prob.v0)
     t = time.perf_counter()
@@ -131,11 +132,11 @@ def run_reference(args):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(n=4)
+        oracle_sample(n=4, smooth=args.smooth)
     vals = []
     t_tot = 0.0
     for _ in range(args.steps):
-        v, dt, nst, desc = oracle_sample(n=args.ref_n)
+        v, dt, nst, desc = oracle_sample(n=args.ref_n, smooth=args.smooth)
         vals.append(v)
         t_tot += dt
     value = float(np.mean(vals))
@@ -160,6 +161,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="cells per direction (profiling runs only)")
     ap.add_argument("--vanka-fp16", type=int, default=0, help="1: FP16 storage of the patch inverses")
+    ap.add_argument("--smooth", type=int, default=SMOOTH["nu1"], help="Vanka pre- and post-sweeps per level")
     ap.add_argument("--serving-requests", type=int, default=16,
                     help="requests of the serving leg (Poisson stream, 20/s); 0 skips it")
     args = ap.parse_args()
@@ -181,7 +183,8 @@ def main():
     w["n"] = args.n
     p = stmg.default_params(dim=w["d"], n_cells_1d=w["n"], r=w["r"], k=w["k"], nu=w["nu"], tau=w["tau"],
                             problem=w["problem"], precond_precision=stmg.STMG_FP32, newton_rtol=1e-10,
-                            newton_atol=ATOL, vanka_fp16=int(args.vanka_fp16), **SMOOTH)
+                            newton_atol=ATOL, vanka_fp16=int(args.vanka_fp16),
+                            **dict(SMOOTH, nu1=args.smooth, nu2=args.smooth))
     stream = torch.cuda.Stream(device=dev)
     S = stmg.Solver(p, inputs.vertices(w["d"], w["n"], w["amp"], w["seed"]), stream=stream.cuda_stream)
     L = S.levels[0]
@@ -277,13 +280,15 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            v, dt, nst, desc = oracle_sample(n=8)
+            v, dt, nst, desc = oracle_sample(n=8, smooth=args.smooth)
             cpu = {"value": v, "unit": "DoF/s", "cores": _cpu_cores(), "kind": "oracle", "sample": desc}
         line = {
             "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "N_st": Nst, "slabs_per_step": 1,
+                       "smoother": {"nu1": args.smooth, "nu2": args.smooth, "omega": "1.2/2^d", "omega_p": 1.0,
+                                    "inverse_storage": "fp16" if args.vanka_fp16 else "fp32"},
                        "l2": "working set larger than L2 (Vanka patch inverses 3.4 GB)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,

@@ -17,7 +17,7 @@ cudaError_t MG<T>::allocate(Handle* hh) {
   nl = (int)h->levels.size();
   U.resize(nl); r.resize(nl); z.resize(nl); t.resize(nl); q.resize(nl); inv.assign(nl, nullptr);
   invh.assign(nl, nullptr); iscale.assign(nl, nullptr);
-  size_t ea = 0, eb = 0, em = 0, nv = 0;
+  size_t ea = 0, eb = 0, em = 0, nv = 0, wk = 0;
   try {
     for (int l = 0; l < nl; ++l) {
       const Level& lv = h->levels[l];
@@ -40,8 +40,10 @@ cudaError_t MG<T>::allocate(Handle* hh) {
         eb = std::max(eb, nc * vanka_elem_size(lv, 1));
         em = std::max(em, nc * vanka_elem_size(lv, 2));
         nv = std::max(nv, (size_t)lv.Nv);
+        wk = std::max(wk, vanka_work_entries(lv, sizeof(T)));
       }
     }
+    if (wk) work = (T*)h->dalloc(wk * sizeof(T));
     if (nl > 1) {
       EA = (T*)h->dalloc(ea * sizeof(T));
       EB = (T*)h->dalloc(eb * sizeof(T));
@@ -103,7 +105,7 @@ cudaError_t MG<T>::setup(const double* U64) {
   }
   for (int l = 0; l + 1 < nl; ++l) {
     h->kbegin(KC_VANKA_BUILD);
-    CKE(vanka_build<T>(h->levels[l], h->pb, U[l], vstar, EA, EB, EM, inv[l], invh[l], iscale[l], status, s));
+    CKE(vanka_build<T>(h->levels[l], h->pb, U[l], vstar, EA, EB, EM, inv[l], invh[l], iscale[l], status, work, s));
     h->kend(KC_VANKA_BUILD, 0.0, 4);
   }
   // coarse: assemble J_c at the coarse state by a batched apply to the identity

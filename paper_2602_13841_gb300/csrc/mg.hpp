@@ -26,6 +26,7 @@ struct MG {
   std::vector<float*> iscale;        // ... with one FP32 scale per patch
   std::vector<Transfer> tr;
   T *EA = nullptr, *EB = nullptr, *EM = nullptr, *vstar = nullptr;
+  T* work = nullptr;                 // global workspace of the large-patch build
   int* status = nullptr;             // device flag: zero pivot in a patch
   int* wstat = nullptr;              // device flag: a bounded wait in the Vanka apply ran out
   cudaError_t check_wait();          // reads and clears wstat (synchronises the stream)
@@ -37,7 +38,7 @@ struct MG {
   float* gj_col = nullptr;
   int* gj_piv = nullptr;
   bool built = false;
-  bool smoothable = true;            // every smoothed level's patch fits on-chip memory
+  bool smoothable = true;            // every smoothed level's element matrices fit on-chip memory
   // The V-cycle of one smoother build is a fixed launch sequence on fixed buffers: it is
   // captured once into a CUDA graph and replayed (launch overhead of the ~40 small launches per
   // level).  Timer spans recorded during the capture are re-read after every replay.
@@ -67,7 +68,8 @@ struct MG {
 // Launch helpers implemented in vanka.cu (templated on T).
 template <typename T>
 cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar, T* EA, T* EB, T* EM,
-                        T* inv, void* invh, float* scale, int* status, cudaStream_t s);
+                        T* inv, void* invh, float* scale, int* status, T* work, cudaStream_t s);
+size_t vanka_work_entries(const Level& lv, size_t esize);  // global build workspace (0: on-chip patches)
 // inv: patch inverses of precision T, or (invh non-null) FP16 inverses scaled by scale[cell].
 template <typename T>
 cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,

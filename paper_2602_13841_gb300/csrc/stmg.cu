@@ -154,7 +154,7 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
   int nn = n, hl = 0;
   while (nn % 2 == 0 && nn / 2 >= 2 && (p->n_levels_h < 0 || hl < p->n_levels_h)) { nn /= 2; ++hl; lv.push_back({nn, r, k}); }
   const double es = p->precond_precision == STMG_FP32 ? 4.0 : 8.0;
-  double tot = 0, ea = 0, eb = 0, em = 0, nvmax = 0;
+  double tot = 0, ea = 0, eb = 0, em = 0, nvmax = 0, wk = 0;
   std::vector<double> nst(lv.size());
   for (size_t l = 0; l < lv.size(); ++l) {
     const int ln = lv[l][0], lr = lv[l][1], lk = lv[l][2];
@@ -170,11 +170,14 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
       const double ent = (lk + 1.0) * msp * st;                          // time-diagonalised inverse
       tot += p->vanka_fp16 ? cells * (ent * 2.0 + 4.0 * (lk + 1.0)) : cells * ent * es;  // patch inverses
       ea = std::max(ea, cells * mv * mv); eb = std::max(eb, cells * npc * mv); em = std::max(em, cells * nl * nl);
+      // patches beyond shared memory are factorised in a global workspace of 304 block slots
+      const double pslot = 2.0 * msp * msp + mv * mv + nl * nl;
+      if (es * (pslot + 2.0 * msp) + 4.0 * msp + 16.0 > 227.0 * 1024.0) wk = std::max(wk, 304.0 * pslot * es);
       nvmax = std::max(nvmax, Nv);
       tot += 3.0 * std::max((lk + 1.0) * Nv, (lk + 1.0) * Np) * es;      // transfer scratch
     }
   }
-  tot += (ea + eb + em + nvmax) * es;
+  tot += (ea + eb + em + nvmax) * es + wk;
   const double Nc = nst.back(), Nb = Nc + lv.back()[2] + 1;
   tot += Nb * Nb * 12.0 + Nc * Nc * 8.0;                                 // coarse factors
   tot += (2.0 * p->gmres_restart + 1.0 + 9.0) * nst[0] * 8.0;           // Krylov basis, Newton vectors

@@ -47,11 +47,32 @@ static size_t elem_smem_any(const Level& lv, size_t es) {
   return N == 3 ? elem_smem<3, 3>(es) : N == 4 ? elem_smem<3, 4>(es) : elem_smem<3, 5>(es);
 }
 
+// The patch matrices of a cell fit shared memory (else k_patch_global, global workspace).
+static bool patch_onchip(const Level& lv, size_t es) { return patch_smem(lv, es) <= 227 * 1024; }
+
+// The stored inverse blob of a cell fits shared memory (else k_vanka_apply_global).
+static bool apply_onchip(const Level& lv, size_t es_store, size_t es) {
+  return apply_smem_bytes(lv.k + 1, (int)vanka_spatial_size(lv), es_store, es) <= 227 * 1024;
+}
+
 bool vanka_supported(const Level& lv, size_t es) {
   const size_t lim = 227 * 1024;
-  const int ms = (int)vanka_spatial_size(lv);
-  return patch_smem(lv, es) <= lim && elem_smem_any(lv, es) <= lim &&
-         apply_smem_bytes(lv.k + 1, ms, es, es) <= lim;
+  const size_t ms = vanka_spatial_size(lv);
+  return elem_smem_any(lv, es) <= lim && es * 2 * ms + sizeof(int) * ms + 16 <= lim;
+}
+
+// Block slots of the global build workspace and their size in entries.
+constexpr int kWorkSlots = 152 * 2;
+static size_t work_slot(const Level& lv) {
+  const size_t ms = vanka_spatial_size(lv);
+  size_t nl = 1;
+  for (int l = 0; l < lv.d; ++l) nl *= (lv.r + 2);
+  const size_t mv = lv.d * nl;
+  return 2 * ms * ms + mv * mv + nl * nl;
+}
+
+size_t vanka_work_entries(const Level& lv, size_t es) {
+  return patch_onchip(lv, es) ? 0 : (size_t)kWorkSlots * work_slot(lv);
 }
 
 // v* = sum_a phi_a(t*) V^a
@@ -66,30 +87,40 @@ __global__ void k_midpoint(const T* __restrict__ U, T* __restrict__ vs, int64_t 
 
 template <typename T, int D, int N>
 static cudaError_t build_dn(const Level& lv, const Problem& pb, const T* U, T* vstar, T* EA, T* EB, T* EM,
-                            T* inv, void* invh, float* scale, int* status, cudaStream_t s) {
+                            T* inv, void* invh, float* scale, int* status, T* work, cudaStream_t s) {
   Tab<T> tb = make_tab<T>(lv.tabs, pb.tau);
   int64_t ncells = lv.Np / lv.npc;
   int64_t g = (lv.Nv + 255) / 256; if (g > 152 * 8) g = 152 * 8;
   k_midpoint<T><<<(int)g, 256, 0, s>>>(U, vstar, lv.Nv, lv.k + 1, tb);
-  VankaArgs<T> V{level_args<T>(lv, pb, 0.0), vstar, EA, EB, EM, inv, (__half*)invh, scale, status};
+  const bool onchip = patch_onchip(lv, sizeof(T));
+  if (!onchip && !work) return cudaErrorInvalidValue;
+  VankaArgs<T> V{level_args<T>(lv, pb, 0.0), vstar, EA, EB, EM, inv, (__half*)invh, scale, status,
+                 onchip ? nullptr : work, onchip ? 0 : (int64_t)work_slot(lv)};
   size_t es = elem_smem<D, N>(sizeof(T));
   cudaError_t e = cudaFuncSetAttribute(k_elem<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)es);
   if (e != cudaSuccess) return e;
   k_elem<T, D, N><<<(unsigned)ncells, 256, es, s>>>(V, tb, ncells);
-  size_t ps = patch_smem(lv, sizeof(T));
-  e = cudaFuncSetAttribute(k_patch<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
-  if (e != cudaSuccess) return e;
-  k_patch<T, D, N><<<(unsigned)ncells, 256, ps, s>>>(V, tb, make_teig<T>(lv.tabs, pb.tau), ncells);
+  if (onchip) {
+    size_t ps = patch_smem(lv, sizeof(T));
+    e = cudaFuncSetAttribute(k_patch<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
+    if (e != cudaSuccess) return e;
+    k_patch<T, D, N><<<(unsigned)ncells, 256, ps, s>>>(V, tb, make_teig<T>(lv.tabs, pb.tau), ncells);
+  } else {
+    const size_t ms = vanka_spatial_size(lv);
+    const size_t ps = sizeof(T) * 2 * ms + sizeof(int) * ms + 16;
+    const int64_t grid = ncells < kWorkSlots ? ncells : kWorkSlots;
+    k_patch_global<T, D, N><<<(unsigned)grid, 512, ps, s>>>(V, tb, make_teig<T>(lv.tabs, pb.tau), ncells);
+  }
   note_launch(3);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar, T* EA, T* EB, T* EM,
-                        T* inv, void* invh, float* scale, int* status, cudaStream_t s) {
+                        T* inv, void* invh, float* scale, int* status, T* work, cudaStream_t s) {
   if (!vanka_supported(lv, sizeof(T))) return cudaErrorNotSupported;
   const int N = lv.r + 2;
-#define STMG_B(DD, NN) return build_dn<T, DD, NN>(lv, pb, U, vstar, EA, EB, EM, inv, invh, scale, status, s)
+#define STMG_B(DD, NN) return build_dn<T, DD, NN>(lv, pb, U, vstar, EA, EB, EM, inv, invh, scale, status, work, s)
   if (lv.d == 2) { if (N == 3) STMG_B(2, 3); if (N == 4) STMG_B(2, 4); if (N == 5) STMG_B(2, 5); }
   else { if (N == 3) STMG_B(3, 3); if (N == 4) STMG_B(3, 4); }
 #undef STMG_B
@@ -103,6 +134,14 @@ static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv
   // one block per cell, threads = spatial patch rows rounded up to whole warps
   const int ms = (int)vanka_spatial_size(lv), kp1 = lv.k + 1;
   const int threads = ((ms + 31) / 32) * 32;
+  if (!apply_onchip(lv, sizeof(SI), sizeof(T))) {
+    const int mr = (ms + 1) & ~1;
+    const size_t gsm = (((size_t)kp1 * mr * sizeof(T) + 7) & ~(size_t)7) + (size_t)ms * 8;
+    k_vanka_apply_global<T, SI, D, N><<<(unsigned)ci.count, threads, gsm, s>>>(
+        level_args<T>(lv, pb, 0.0), inv, scale, res, d, (T)omega, (T)omega_p, kp1, lv.npc,
+        make_teig<T>(lv.tabs, pb.tau), ci);
+    return cudaSuccess;
+  }
   const size_t smem = apply_smem_bytes(kp1, ms, sizeof(SI), sizeof(T));
   cudaError_t e = cudaFuncSetAttribute(k_vanka_apply<T, SI, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -144,9 +183,9 @@ cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const 
 }
 
 template cudaError_t vanka_build<float>(const Level&, const Problem&, const float*, float*, float*, float*, float*,
-                                        float*, void*, float*, int*, cudaStream_t);
+                                        float*, void*, float*, int*, float*, cudaStream_t);
 template cudaError_t vanka_build<double>(const Level&, const Problem&, const double*, double*, double*, double*,
-                                         double*, double*, void*, float*, int*, cudaStream_t);
+                                         double*, double*, void*, float*, int*, double*, cudaStream_t);
 template cudaError_t vanka_apply<float>(const Level&, const Problem&, const float*, const void*, const float*,
                                         const float*, float*, double, double, int, int*, cudaStream_t);
 template cudaError_t vanka_apply<double>(const Level&, const Problem&, const double*, const void*, const float*,

@@ -36,6 +36,8 @@ struct VankaArgs {
   __half* invh;         // the same scaled to [-1, 1] in FP16 with one FP32 factor per block
   float* scale;         // [cells][nblk]
   int* status;          // set to 1 on a zero pivot
+  T* work;              // global workspace of k_patch_global (null for on-chip patches) ...
+  int64_t wslot;        // ... entries per block slot
 };
 
 // Column stride of a stored patch inverse: m rounded up to 8 entries (16-byte aligned columns).
@@ -423,21 +425,12 @@ __device__ bool gauss_jordan_c(T* Sr, T* Si, int m, int* piv_row, T* cr, T* ci) 
 // it is similar to the block diagonal of T_lam = [lam M + A, B^T; B, 0]: one spatial inverse
 // per eigenvalue instead of one inverse of the whole space-time patch (Sec. 4.3).
 template <typename T, int D, int N>
-__global__ void k_patch(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t ncells) {
+__device__ bool patch_cell(const VankaArgs<T>& V, const Tab<T>& tb, const TEig<T>& te, int64_t cell, T* Sr, T* Si,
+                           T* Ap, T* Mp, T* cr, T* ci, int* piv) {
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int npc = tb.npc, kp1 = tb.k + 1;
   const int ms = MV + npc, st = inv_stride(ms);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Sr = reinterpret_cast<T*>(smem_raw);           // [ms][ms]
-  T* Si = Sr + ms * ms;                             // [ms][ms] imaginary part
-  T* Ap = Si + ms * ms;                             // [MV][MV] assembled velocity block
-  T* Mp = Ap + MV * MV;                             // [NL][NL] assembled scalar mass
-  T* cr = Mp + NL * NL;                             // [ms]
-  T* ci = cr + ms;                                  // [ms]
-  int* piv = reinterpret_cast<int*>(ci + ms);       // [ms]
-  const int64_t cell = blockIdx.x;
-  if (cell >= ncells) return;
   const LevelArgs<T>& L = V.L;
   int cc[3] = {0, 0, 0};
   cell_coords<D>(cell, L.n, cc);
@@ -512,7 +505,7 @@ __global__ void k_patch(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t ncells) {
     }
     __syncthreads();
     const bool ok = cplx ? gauss_jordan_c<T>(Sr, Si, ms, piv, cr, ci) : gauss_jordan<T>(Sr, ms, ms, piv, cr);
-    if (!ok) { if (tid == 0) *V.status = 1; return; }
+    if (!ok) { if (tid == 0) *V.status = 1; return false; }
     const int w = cplx ? 2 : 1;                                  // reals per stored entry
     const int64_t bbase = cbase + (int64_t)te.off[e] * ms * st;  // in reals
     if (V.invh) {
@@ -539,6 +532,48 @@ __global__ void k_patch(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t ncells) {
         if (cplx) inv[(int64_t)w * ent + 1] = in ? Si[i * ms + j] : (T)0;
       }
     }
+    __syncthreads();
+  }
+  return true;
+}
+
+// Patches whose matrices fit shared memory: one block per cell.
+template <typename T, int D, int N>
+__global__ void k_patch(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t ncells) {
+  constexpr int NL = Shape<D, N>::Q;
+  constexpr int MV = D * NL;
+  const int ms = MV + tb.npc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Sr = reinterpret_cast<T*>(smem_raw);           // [ms][ms]
+  T* Si = Sr + ms * ms;                             // [ms][ms] imaginary part
+  T* Ap = Si + ms * ms;                             // [MV][MV] assembled velocity block
+  T* Mp = Ap + MV * MV;                             // [NL][NL] assembled scalar mass
+  T* cr = Mp + NL * NL;                             // [ms]
+  T* ci = cr + ms;                                  // [ms]
+  int* piv = reinterpret_cast<int*>(ci + ms);       // [ms]
+  const int64_t cell = blockIdx.x;
+  if (cell >= ncells) return;
+  patch_cell<T, D, N>(V, tb, te, cell, Sr, Si, Ap, Mp, cr, ci, piv);
+}
+
+// Larger patches (3D, r >= 2): the matrices live in a per-block slot of a global workspace
+// (V.work, V.wslot entries per slot; the slots together stay L2-resident); blocks stride over
+// the cells.  Only the pivot bookkeeping is in shared memory.
+template <typename T, int D, int N>
+__global__ void k_patch_global(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t ncells) {
+  constexpr int NL = Shape<D, N>::Q;
+  constexpr int MV = D * NL;
+  const int ms = MV + tb.npc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* cr = reinterpret_cast<T*>(smem_raw);           // [ms]
+  T* ci = cr + ms;                                  // [ms]
+  int* piv = reinterpret_cast<int*>(ci + ms);       // [ms]
+  T* Sr = V.work + (int64_t)blockIdx.x * V.wslot;
+  T* Si = Sr + ms * ms;
+  T* Ap = Si + ms * ms;
+  T* Mp = Ap + MV * MV;
+  for (int64_t cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
+    if (!patch_cell<T, D, N>(V, tb, te, cell, Sr, Si, Ap, Mp, cr, ci, piv)) return;
     __syncthreads();
   }
 }
@@ -682,6 +717,100 @@ __global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const 
       const T* r1 = r0 + mr;
       for (int j = 0; j < ms; ++j) {
         const auto v = InvLd<SI>::cx(blk + 2 * (j * st + i));
+        const T vr = (T)v.x, vi = (T)v.y, xr = r0[j], xi = r1[j];
+        ar += vr * xr - vi * xi;
+        ai += vr * xi + vi * xr;
+      }
+    }
+    const T sc = scale ? (T)scale[cell * te.nblk + e] : (T)1;
+#pragma unroll
+    for (int q = 0; q < MAXKP1; ++q)
+      if (q == e) { yr[q] = sc * ar; yi[q] = sc * ai; }
+  }
+  const int64_t g = gb[i];
+  const int64_t sa = i < MV ? L.Nv : L.Np;
+  const T wgt = i < MV ? omega : omega_p;
+  for (int a = 0; a < kp1; ++a) {
+    T y = 0;
+#pragma unroll
+    for (int e = 0; e < MAXKP1; ++e)
+      if (e < te.nblk) y += te.Gre[a][e] * yr[e] - te.Gim[a][e] * yi[e];
+    d[g + a * sa] += wgt * y;
+  }
+}
+
+// Patches whose inverse blob exceeds shared memory (3D, r >= 2): the same arithmetic as
+// k_vanka_apply, each thread streaming its row of every block straight from global memory.
+template <typename SI> struct InvLdG;
+template <> struct InvLdG<float> {
+  __device__ static float re(const float* p) { return __ldg(p); }
+  __device__ static float2 cx(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+};
+template <> struct InvLdG<double> {
+  __device__ static double re(const double* p) { return __ldg(p); }
+  __device__ static double2 cx(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
+};
+template <> struct InvLdG<__half> {
+  __device__ static float re(const __half* p) { return __half2float(__ldg(p)); }
+  __device__ static float2 cx(const __half* p) { return __half22float2(__ldg(reinterpret_cast<const __half2*>(p))); }
+};
+
+template <typename T, typename SI, int D, int N>
+__global__ void k_vanka_apply_global(LevelArgs<T> L, const SI* __restrict__ inv, const float* __restrict__ scale,
+                                     const T* __restrict__ res, T* __restrict__ d, T omega, T omega_p, int kp1,
+                                     int npc, TEig<T> te, ColorInfo ci) {
+  constexpr int NL = Shape<D, N>::Q;
+  constexpr int MV = D * NL;
+  const int ms = MV + npc, st = inv_stride(ms), mr = (ms + 1) & ~1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* rt = reinterpret_cast<T*>(smem_raw);                                              // [kp1 units][mr]
+  int64_t* gb = reinterpret_cast<int64_t*>(smem_raw + (((size_t)kp1 * mr * sizeof(T) + 7) & ~(size_t)7));
+  const int cidx = blockIdx.x;
+  if (cidx >= ci.count) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int cc[3] = {0, 0, 0};
+  decode_color_cell<D>(ci, cidx, cc);
+  int64_t cell = 0, s = 1;
+  for (int l = 0; l < D; ++l) { cell += (int64_t)cc[l] * s; s *= L.n; }
+  for (int l = tid; l < ms; l += nt) {
+    int64_t g, sa;
+    if (l < MV) {
+      const int c = l / NL, i = l % NL;
+      g = c * L.nnodes + global_node<D>(L.N1, cc, N - 1, i, N);
+      sa = L.Nv;
+    } else {
+      g = (int64_t)kp1 * L.Nv + cell * npc + (l - MV);
+      sa = L.Np;
+    }
+    gb[l] = g;
+    T ra[MAXKP1];
+#pragma unroll
+    for (int a = 0; a < MAXKP1; ++a) ra[a] = a < kp1 ? res[g + a * sa] : (T)0;
+    for (int e = 0; e < te.nblk; ++e) {
+      T fr = 0, fi = 0;
+#pragma unroll
+      for (int a = 0; a < MAXKP1; ++a) { fr += te.Fre[e][a] * ra[a]; fi += te.Fim[e][a] * ra[a]; }
+      rt[te.off[e] * mr + l] = fr;
+      if (te.cplx[e]) rt[(te.off[e] + 1) * mr + l] = fi;
+    }
+  }
+  __syncthreads();
+  const int i = tid;
+  if (i >= ms) return;
+  const SI* base = inv + cell * (int64_t)kp1 * ms * st;
+  T yr[MAXKP1], yi[MAXKP1];
+#pragma unroll
+  for (int e = 0; e < MAXKP1; ++e) { yr[e] = 0; yi[e] = 0; }
+  for (int e = 0; e < te.nblk; ++e) {
+    const SI* blk = base + (int64_t)te.off[e] * ms * st;
+    const T* r0 = rt + te.off[e] * mr;
+    T ar = 0, ai = 0;
+    if (!te.cplx[e]) {
+      for (int j = 0; j < ms; ++j) ar += (T)InvLdG<SI>::re(blk + (int64_t)j * st + i) * r0[j];
+    } else {
+      const T* r1 = r0 + mr;
+      for (int j = 0; j < ms; ++j) {
+        const auto v = InvLdG<SI>::cx(blk + 2 * ((int64_t)j * st + i));
         const T vr = (T)v.x, vi = (T)v.y, xr = r0[j], xi = r1[j];
         ar += vr * xr - vi * xi;
         ai += vr * xi + vi * xr;

@@ -38,22 +38,37 @@ cudaError_t vcopy(int64_t n, const S* x, T* y, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Partial dot products of up to DOTS_PER_ROW basis vectors with w per block: w[i] is read once
+// for all of them.  Each thread accumulates its strided elements in index order, then the block
+// reduces in a fixed tree: the result does not depend on how many vectors share a block.
+constexpr int DOTS_PER_ROW = 4;
+
 template <typename T>
-__global__ void k_dots_partial(int64_t n, const T* __restrict__ X, int64_t ldx, const T* __restrict__ w,
+__global__ void k_dots_partial(int64_t n, int m, const T* __restrict__ X, int64_t ldx, const T* __restrict__ w,
                                double* __restrict__ part) {
-  __shared__ double red[RED_THREADS];
-  const int l = blockIdx.y;
-  const T* x = X + l * ldx;
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)RED_BLOCKS * RED_THREADS)
-    acc += (double)x[i] * (double)w[i];
-  red[threadIdx.x] = acc;
+  __shared__ double red[DOTS_PER_ROW][RED_THREADS];
+  const int l0 = blockIdx.y * DOTS_PER_ROW;
+  const int cnt = m - l0 < DOTS_PER_ROW ? m - l0 : DOTS_PER_ROW;
+  double acc[DOTS_PER_ROW] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t stride = (int64_t)RED_BLOCKS * RED_THREADS;
+  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += stride) {
+    const double wi = (double)w[i];
+    double xv[DOTS_PER_ROW];
+#pragma unroll
+    for (int q = 0; q < DOTS_PER_ROW; ++q) xv[q] = q < cnt ? (double)X[(l0 + q) * ldx + i] : 0.0;
+#pragma unroll
+    for (int q = 0; q < DOTS_PER_ROW; ++q) acc[q] += xv[q] * wi;
+  }
+#pragma unroll
+  for (int q = 0; q < DOTS_PER_ROW; ++q) red[q][threadIdx.x] = acc[q];
   __syncthreads();
   for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int q = 0; q < DOTS_PER_ROW; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[l * RED_BLOCKS + blockIdx.x] = red[0];
+  if (threadIdx.x < cnt) part[(l0 + threadIdx.x) * RED_BLOCKS + blockIdx.x] = red[threadIdx.x][0];
 }
 
 __global__ void k_dots_final(const double* __restrict__ part, double* __restrict__ out) {
@@ -74,7 +89,8 @@ template <typename T>
 cudaError_t vdots(int64_t n, int m, const T* X, int64_t ldx, const T* w, double* out, double* scratch,
                   cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
-  k_dots_partial<T><<<dim3(RED_BLOCKS, m), RED_THREADS, 0, s>>>(n, X, ldx, w, scratch);
+  k_dots_partial<T><<<dim3(RED_BLOCKS, (m + DOTS_PER_ROW - 1) / DOTS_PER_ROW), RED_THREADS, 0, s>>>(n, m, X, ldx, w,
+                                                                                              scratch);
   note_launch();
   k_dots_final<<<m, RED_THREADS, 0, s>>>(scratch, out);
   return cudaGetLastError();
@@ -88,6 +104,7 @@ __global__ void k_sub_comb(int64_t n, int m, const T* __restrict__ X, int64_t ld
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double acc = (double)w[i];
+#pragma unroll 8
     for (int l = 0; l < m; ++l) acc -= hs[l] * (double)X[l * ldx + i];
     w[i] = (T)acc;
   }

@@ -71,7 +71,9 @@ def test_transfers_match_oracle(d, n, r, k, amp, prec):
 
 @pytest.mark.parametrize("d,n,r,k,amp,prec", [(2, 8, 2, 2, 0.15, "fp64"), (2, 8, 1, 1, 0.0, "fp64"),
                                               (2, 6, 1, 0, 0.1, "fp64"), (2, 8, 2, 2, 0.15, "fp32"),
-                                              (3, 4, 1, 1, 0.1, "fp32")])
+                                              (3, 4, 1, 1, 0.1, "fp32"),
+                                              # 3D Q3/P2: patches beyond shared memory (global path)
+                                              (3, 2, 2, 1, 0.1, "fp64"), (3, 4, 2, 1, 0.0, "fp32")])
 def test_smoother_and_vcycle_match_oracle(d, n, r, k, amp, prec):
     """FP64: tight tolerances.  FP32 (the mixed-precision preconditioner): the error of each
     result against the FP64 oracle is bounded by 2e-3 relative (ill-conditioned patches)."""
@@ -115,6 +117,8 @@ def test_smoother_and_vcycle_match_oracle(d, n, r, k, amp, prec):
     ("fp32", 2, 8, 1, 2, 0.1, 1e-2, 0.1, "MMS2D"),
     ("fp32", 3, 4, 1, 1, 0.1, 1.0 / 400, 0.05, "TG3D"),
     ("fp32", 3, 4, 1, 0, 0.0, 1e-2, 0.05, "MMS3D"),
+    ("fp32", 3, 4, 1, 2, 0.1, 1.0 / 400, 0.01, "MMS3D"),   # small case of the 3D Q2/P1/DG(2) workload
+    ("fp32", 3, 4, 2, 1, 0.0, 1.0 / 1600, 0.02, "TG3D"),   # small case of the 3D Q3/P2/DG(1) workload
 ])
 def test_slab_solve_reaches_tolerance_and_matches_exact_solution(precision, d, n, r, k, amp, nu, tau, pname):
     import torch
