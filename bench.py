@@ -213,9 +213,9 @@ def main():
     torch.cuda.synchronize(dev)
     lib = stmg.load()
     launches0 = lib.stmg_launch_count()
-    # phase timers plus the timer of the dominant kernel class only (Vanka patch apply, class
-    # 3): every timed launch adds two event nodes to the V-cycle graph
-    S.set_timing(True, classes=(3,))
+    # phase timers plus the timer of the dominant kernel only (finest-level Vanka patch apply,
+    # class 6): every timed span adds two event nodes to the V-cycle graph
+    S.set_timing(True, classes=(6,))
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stats = []
     if ws > 1:
@@ -254,10 +254,20 @@ def main():
         e2e = {"value": ws * Nst * args.steps / (ms_e2e * 1e-3), "unit": "DoF/s",
                "h2d_bytes_per_step": Nv * 8, "d2h_bytes_per_step": Nst * 8}
 
-    # ---- roofline of the dominant kernel (Vanka patch apply, HBM-bound) from the live timers
-    prof = S.kernel_profile()
-    roof = roofline(S, prof)
-    buckets = {key: float(np.sum([st[key] for st in stats])) for key in ("t_rebuild", "t_vanka", "t_mg_other", "t_other")}
+    # ---- roofline of the dominant kernel (finest-level Vanka apply, HBM-bound) from the live
+    # timers of the timed region
+    prof = S.kernel_profile(reset=True)
+    roof = roofline(S, prof, args)
+    # ---- breakdown (outside the timed region): one more slab with every kernel class timed, for
+    # the paper's four phases (rebuild Vanka, apply Vanka, rest of MG, other) and the class shares
+    S.set_timing(True)
+    pstats = []
+    with torch.cuda.stream(stream):
+        march(1, None, pstats)
+    torch.cuda.synchronize(dev)
+    S.set_timing(False)
+    pprof = S.kernel_profile()
+    buckets = {key: float(pstats[0][key]) for key in ("t_rebuild", "t_vanka", "t_mg_other", "t_other")}
     peaks = _peaks()
     S.close()
     serving = None
@@ -300,7 +310,8 @@ def main():
                        "gmres_its": [st["gmres_its_total"] for st in stats],
                        "rebuilds": [st["rebuilds"] for st in stats],
                        "res_ratio": [st["res_final"] / st["res0"] for st in stats]},
-            "phase_seconds": buckets, "kernels": {c: v for c, v in prof.items() if v["count"]}, "peaks": peaks, "serving": serving,
+            "breakdown_one_slab": {"phase_seconds": buckets,
+                                   "kernels": {c: v for c, v in pprof.items() if v["count"]}}, "peaks": peaks, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -329,17 +340,32 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
-def roofline(S, prof):
-    """Vanka patch apply: per colour launch it reads the patch inverses of its cells (m_st^2
-    values), the residual and the correction on the patch DoFs, and writes the correction."""
+# DRAM bytes (read + write) per cell of the finest-level Vanka apply, FP32 inverses, Q3/P2/DG(2):
+# ncu capture of one colour launch on the 192^2 mesh of the same recipe, 188.17 MB for 9216
+# cells (profiles/k_vanka_apply_2d_192sq_q3p2_dg2_fp32.md); scaled to a 256^2 launch by its cells.
+VANKA_DRAM_BYTES_PER_CELL = 188.167168e6 / 9216
+
+
+def roofline(S, prof, args):
+    """Finest-level Vanka patch apply (the dominant kernel): per colour launch it reads the
+    time-diagonalised patch inverses of its cells ((k+1) m_s^2 reals each), gathers the residual
+    and reads and writes the correction on the patch DoFs.  Achieved = those algorithmic bytes
+    per launch over the launch's average device time (CUDA events on the solver stream)."""
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    k = prof.get("vanka_apply")
+    k = prof.get("vanka_apply_finest")
     if not k or not k["count"]:
         return None
-    return {"bound": "hbm", "kernel": "k_vanka_apply", "achieved": k["bytes"] / (k["ms"] * 1e-3) / 1e9,
-            "peak": hbm, "unit": "GB/s", "frac": k["bytes"] / (k["ms"] * 1e-3) / 1e9 / hbm,
-            "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+    achieved = k["bytes"] / (k["ms"] * 1e-3) / 1e9
+    cells = (args.n // 2) ** 2                     # cells of one colour launch on the finest level
+    traffic = (VANKA_DRAM_BYTES_PER_CELL * cells
+               if (args.vanka_fp16 == 0 and WORKLOAD["d"] == 2 and WORKLOAD["r"] == 2 and WORKLOAD["k"] == 2)
+               else None)
+    return {"bound": "hbm", "kernel": "k_vanka_apply (finest level)", "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+            "algorithmic_bytes_per_launch": k["bytes"] / k["count"],
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+            "traffic_source": "ncu 192^2 capture scaled by cells per launch" if traffic else None,
             "launches": k["count"], "avg_us": 1e3 * k["ms"] / k["count"]}
 
 

@@ -204,7 +204,8 @@ stmg_status stmg_set_timing_classes(stmg_handle* h, unsigned mask);
  * on (collected at the end of each stmg_slab_solve).  Classes: 0 FP64 Jacobian apply (outer
  * FGMRES), 1 preconditioner-precision Jacobian apply (level residuals), 2 residual, 3 Vanka
  * patch apply (one launch per colour; bytes = patch inverses + patch vectors), 4 Vanka build
- * (element matrices, patch assembly and inversion), 5 mass apply. */
+ * (element matrices, patch assembly and inversion), 5 mass apply, 6 Vanka patch apply on the
+ * finest level only (a subset of class 3). */
 stmg_status stmg_kernel_profile(const stmg_handle* h, int cls, double* ms, long long* launches,
                                 double* bytes);
 stmg_status stmg_kernel_profile_reset(stmg_handle* h);

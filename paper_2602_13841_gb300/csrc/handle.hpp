@@ -17,7 +17,7 @@ namespace stmg {
 // Kernel classes of the profile: FP64 Jacobian apply, preconditioner-precision Jacobian apply,
 // residual, Vanka patch apply (one launch per colour), Vanka build, mass apply.
 enum KernelClass { KC_APPLY64 = 0, KC_APPLYP = 1, KC_RESIDUAL = 2, KC_VANKA_APPLY = 3, KC_VANKA_BUILD = 4,
-                   KC_MASS = 5, KC_COUNT = 6 };
+                   KC_MASS = 5, KC_VANKA_APPLY0 = 6, KC_COUNT = 7 };
 
 // Accumulates device time of one phase from CUDA event pairs recorded on the handle's stream.
 struct PhaseTimer {

@@ -167,10 +167,12 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
     const double ib = (lv.k + 1) * ms * ms * (invh[l] ? 2.0 : (double)sizeof(T)) + (invh[l] ? 4.0 * (lv.k + 1) : 0.0);
     int64_t cells = 0;
     h->kbegin(KC_VANKA_APPLY);
+    if (l == 0) h->kbegin(KC_VANKA_APPLY0);
     for (int c = 0; c < lv.ncolors; ++c) {
       CKE(vanka_apply<T>(lv, h->pb, inv[l], invh[l], iscale[l], res, d, omega, h->prm.omega_p, c, wstat, s));
       cells += lv.colors[c].count;
     }
+    if (l == 0) h->kend(KC_VANKA_APPLY0, (double)cells * (ib + 3.0 * m * sizeof(T)), lv.ncolors);
     h->kend(KC_VANKA_APPLY, (double)cells * (ib + 3.0 * m * sizeof(T)), lv.ncolors);
   }
   return cudaSuccess;

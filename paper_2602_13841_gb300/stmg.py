@@ -254,7 +254,8 @@ class Solver:
         self._check(self.lib.stmg_set_physics(self.h, float(nu), float(tau), int(problem)), "set_physics")
         self.params.nu, self.params.tau, self.params.problem = nu, tau, problem
 
-    KERNEL_CLASSES = ("apply_fp64", "apply_precond", "residual", "vanka_apply", "vanka_build", "mass")
+    KERNEL_CLASSES = ("apply_fp64", "apply_precond", "residual", "vanka_apply", "vanka_build", "mass",
+                      "vanka_apply_finest")
 
     def kernel_profile(self, reset=False):
         """{class: {ms, count, bytes}} accumulated while timing was on."""
