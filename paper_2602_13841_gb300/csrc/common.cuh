@@ -23,6 +23,20 @@ struct Tab {
   int k, npc, r;
 };
 
+// Opt-in dynamic shared memory of a kernel.  The attribute belongs to the function and is shared
+// by every handle in the process, so it is always set to the device maximum: a per-launch value
+// would race between handles on different host threads (one thread lowering the cap between
+// another thread's set and launch).  Returns cudaErrorInvalidValue if `bytes` exceeds it.
+template <typename F>
+inline cudaError_t allow_smem(F* func, size_t bytes) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (bytes > (size_t)optin) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
 // Time diagonalisation of the Vanka patch for a slab of length tau (see LevelTables): block e
 // has eigenvalue lam_e = (2/tau) mu_e of W^{-1} K, forward row F[e][a] = (2/tau) (Q^{-1}
 // Omega^{-1})[e][a] and backward column G[a][e] (x2 for a complex block, whose conjugate

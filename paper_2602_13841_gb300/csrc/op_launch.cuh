@@ -44,13 +44,13 @@ static cudaError_t launch_dn(const Level& lv, const Problem& pb, double t0, cons
   int cpb = 256 / Q; if (cpb < 1) cpb = 1;
   int smem = cpb * vol_smem_per_cell<T, D, N, MODE>(kp1);
   while (smem > 160 * 1024 && cpb > 1) { --cpb; smem = cpb * vol_smem_per_cell<T, D, N, MODE>(kp1); }
-  cudaError_t e = cudaFuncSetAttribute(k_volume<T, D, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = allow_smem(k_volume<T, D, N, MODE>, (size_t)smem);
   if (e != cudaSuccess) return e;
   int fcpb = 256 / Q; if (fcpb < 1) fcpb = 1;
   int fsmem = fcpb * face_smem_per_cell<T, D, N>(kp1);
   while (fsmem > 160 * 1024 && fcpb > 1) { --fcpb; fsmem = fcpb * face_smem_per_cell<T, D, N>(kp1); }
   if (MODE != MM) {
-    e = cudaFuncSetAttribute(k_faces<T, D, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem);
+    e = allow_smem(k_faces<T, D, N, MODE>, (size_t)fsmem);
     if (e != cudaSuccess) return e;
   }
   for (int b = 0; b < batch; ++b) {

@@ -97,12 +97,12 @@ static cudaError_t build_dn(const Level& lv, const Problem& pb, const T* U, T* v
   VankaArgs<T> V{level_args<T>(lv, pb, 0.0), vstar, EA, EB, EM, inv, (__half*)invh, scale, status,
                  onchip ? nullptr : work, onchip ? 0 : (int64_t)work_slot(lv)};
   size_t es = elem_smem<D, N>(sizeof(T));
-  cudaError_t e = cudaFuncSetAttribute(k_elem<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)es);
+  cudaError_t e = allow_smem(k_elem<T, D, N>, es);
   if (e != cudaSuccess) return e;
   k_elem<T, D, N><<<(unsigned)ncells, 256, es, s>>>(V, tb, ncells);
   if (onchip) {
     size_t ps = patch_smem(lv, sizeof(T));
-    e = cudaFuncSetAttribute(k_patch<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
+    e = allow_smem(k_patch<T, D, N>, ps);
     if (e != cudaSuccess) return e;
     k_patch<T, D, N><<<(unsigned)ncells, 256, ps, s>>>(V, tb, make_teig<T>(lv.tabs, pb.tau), ncells);
   } else {
@@ -143,8 +143,7 @@ static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv
     return cudaSuccess;
   }
   const size_t smem = apply_smem_bytes(kp1, ms, sizeof(SI), sizeof(T));
-  cudaError_t e = cudaFuncSetAttribute(k_vanka_apply<T, SI, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_smem(k_vanka_apply<T, SI, D, N>, smem);
   if (e != cudaSuccess) return e;
   k_vanka_apply<T, SI, D, N><<<(unsigned)ci.count, threads, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, scale, res, d,
                                                                        (T)omega, (T)omega_p, kp1, lv.npc,

@@ -128,6 +128,8 @@ class Server:
             S.initial_condition(V0)
             S.initial_guess(V0, U)
             rc, st = S.slab_solve(0.0, V0, U, check=False)
+            if rc != 0:
+                st["error"] = S.lib.stmg_last_error(S.h).decode()
             chk = float(U.abs().sum().item())
             sol = U.cpu().numpy() if self.keep else None
             torch.cuda.current_stream().synchronize()

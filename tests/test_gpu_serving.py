@@ -14,7 +14,10 @@ def test_mixed_stream_results_equal_solo_results():
     from paper_2602_13841_gb300.serving import Request, Server, report
     reqs = [Request(0, 2, 16, 1, 1, 150.0, "TG2D"), Request(1, 2, 8, 2, 2, 900.0, "MMS2D"),
             Request(2, 2, 16, 1, 1, 1200.0, "MMS2D"), Request(3, 3, 4, 1, 1, 400.0, "TG3D"),
-            Request(4, 2, 12, 3, 0, 300.0, "TG2D"), Request(5, 2, 16, 1, 1, 700.0, "TG2D")]
+            Request(4, 2, 12, 3, 0, 300.0, "TG2D"), Request(5, 2, 16, 1, 1, 700.0, "TG2D"),
+            # 3D shapes whose kernels share template instances with different shared-memory needs
+            Request(6, 3, 4, 1, 2, 500.0, "MMS3D"), Request(7, 3, 4, 1, 0, 300.0, "TG3D"),
+            Request(8, 3, 4, 2, 1, 800.0, "TG3D")]
     mix = Server(workers=3, keep_solutions=True)
     res = mix.run(reqs, realtime=False)
     mix.close()
