@@ -26,15 +26,20 @@ struct Tab {
 // Opt-in dynamic shared memory of a kernel.  The attribute belongs to the function and is shared
 // by every handle in the process, so it is always set to the device maximum: a per-launch value
 // would race between handles on different host threads (one thread lowering the cap between
-// another thread's set and launch).  Returns cudaErrorInvalidValue if `bytes` exceeds it.
+// another thread's set and launch).  The cap is the opt-in maximum less the kernel's static
+// shared memory; returns cudaErrorInvalidValue if `bytes` exceeds it.
 template <typename F>
 inline cudaError_t allow_smem(F* func, size_t bytes) {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  if (bytes > (size_t)optin) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  const size_t cap = (size_t)optin - fa.sharedSizeBytes;     // static shared memory counts too
+  if (bytes > cap) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
 }
 
 // Time diagonalisation of the Vanka patch for a slab of length tau (see LevelTables): block e
