@@ -279,10 +279,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_volume2d(OpArgs
     v = shfl_x<T, N>(u[c], sB, tx, cb + ty * N, false);
     uq[c] = shfl_y<T, N>(v, sB, ty, cb + tx, false);
   }
-  // cell volume |K| (for h_{Gamma_D} of boundary faces)
+  // cell volume |K| (for h_{Gamma_D} of boundary faces), needed only where a group has a face
+  const bool bcell = on && (cc[0] == 0 || cc[1] == 0 || cc[0] == L.n - 1 || cc[1] == L.n - 1);
   T vol = 0;
+  if (MODE != MM && __any_sync(0xffffffffu, bcell)) {
 #pragma unroll
-  for (int q = 0; q < Q; ++q) vol += __shfl_sync(0xffffffffu, JxW, cb + q);
+    for (int q = 0; q < Q; ++q) vol += __shfl_sync(0xffffffffu, JxW, cb + q);
+  }
   // pressure at this quadrature point
   T pq = 0;
 #pragma unroll
@@ -341,10 +344,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_volume2d(OpArgs
   // pressure test functions: lane cb + m accumulates sum_t psi_m(t) sp(t)
   T pacc = 0;
   const int mo = t < npc ? t : 0;
+  const int mx = tb.modes[mo][0], my = tb.modes[mo][1];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     T sv = __shfl_sync(0xffffffffu, sp, cb + q);
-    pacc += sP1[q % N][tb.modes[mo][0]] * sP1[q / N][tb.modes[mo][1]] * sv;
+    pacc += sP1[q % N][mx] * sP1[q / N][my] * sv;
   }
   // boundary faces (Nitsche, boundary convection) of boundary cells
   if (MODE != MM) {
