@@ -22,6 +22,8 @@ struct Level {
   int nbcells[8]{};
   int ncolors = 0;
   double hscale = 0;                  // Nitsche length factor (see LevelArgs)
+  double* geo64 = nullptr;            // 2D: geometry table of the Jacobian apply (see OpArgs::geo)
+  float* geo32 = nullptr;
 };
 
 struct Problem {
@@ -43,5 +45,9 @@ cudaError_t launch_operator(const Level& lv, const Problem& pb, int mode, double
                             int batch = 1, int64_t xs = 0, int64_t ys = 0);
 
 cudaError_t launch_initial_condition(const Level& lv, const Problem& pb, double* V0, cudaStream_t s);
+
+// Fill lv.geo64 / lv.geo32 (allocated by the caller: cells x 5 x (r+2)^2 entries each) for a 2D
+// level.
+cudaError_t build_geometry(const Level& lv, const Problem& pb, cudaStream_t s);
 
 }  // namespace stmg

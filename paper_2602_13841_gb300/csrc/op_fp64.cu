@@ -50,4 +50,23 @@ cudaError_t launch_initial_condition(const Level& lv, const Problem& pb, double*
   return cudaGetLastError();
 }
 
+template <typename T, int N>
+static void geo_launch(const Level& lv, const Problem& pb, T* geo, cudaStream_t s) {
+  const int64_t ncells = (int64_t)lv.n * lv.n;
+  int64_t blocks = (ncells * N * N + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_geo2d<T, N><<<(unsigned)blocks, 256, 0, s>>>(level_args<T>(lv, pb, 0.0), make_tab<T>(lv.tabs, pb.tau), geo,
+                                                 ncells);
+  note_launch();
+}
+
+cudaError_t build_geometry(const Level& lv, const Problem& pb, cudaStream_t s) {
+  if (lv.d != 2 || !lv.geo64 || !lv.geo32) return cudaErrorInvalidValue;
+  const int N = lv.r + 2;
+#define STMG_G(NN) { geo_launch<double, NN>(lv, pb, lv.geo64, s); geo_launch<float, NN>(lv, pb, lv.geo32, s); }
+  if (N == 3) STMG_G(3) else if (N == 4) STMG_G(4) else if (N == 5) STMG_G(5) else return cudaErrorInvalidValue;
+#undef STMG_G
+  return cudaGetLastError();
+}
+
 }  // namespace stmg

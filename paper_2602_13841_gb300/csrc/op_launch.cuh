@@ -1,5 +1,6 @@
 // Launch helpers for the operator kernels (included by the per-precision translation units).
 #pragma once
+#include <type_traits>
 #include "level.hpp"
 #include "operator.cuh"
 #include "operator2d.cuh"
@@ -40,7 +41,11 @@ static cudaError_t launch_dn(const Level& lv, const Problem& pb, double t0, cons
   constexpr int Q = Shape<D, N>::Q;
   const int kp1 = lv.k + 1;
   Tab<T> tb = make_tab<T>(lv.tabs, pb.tau);
-  OpArgs<T> A{level_args<T>(lv, pb, t0), x, state, vprev, y, xs, ys};
+  const T* geo = nullptr;
+  if constexpr (D == 2) {
+    if constexpr (std::is_same<T, double>::value) geo = lv.geo64; else geo = lv.geo32;
+  }
+  OpArgs<T> A{level_args<T>(lv, pb, t0), x, state, vprev, y, xs, ys, geo};
   int cpb = 256 / Q; if (cpb < 1) cpb = 1;
   int smem = cpb * vol_smem_per_cell<T, D, N, MODE>(kp1);
   while (smem > 160 * 1024 && cpb > 1) { --cpb; smem = cpb * vol_smem_per_cell<T, D, N, MODE>(kp1); }

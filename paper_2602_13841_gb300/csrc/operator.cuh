@@ -69,6 +69,8 @@ struct OpArgs {
   const T* vprev;    // R: V_{n-1}
   T* y;              // output (accumulated)
   int64_t xs, ys;    // batch strides (blockIdx.y selects the column of a batched apply)
+  const T* geo;      // 2D: per cell [5][Q] inverse Jacobian G[0][0], G[0][1], G[1][0], G[1][1] and
+                     // JxW at the quadrature points (precomputed at set-up), or null
 };
 
 template <int D>

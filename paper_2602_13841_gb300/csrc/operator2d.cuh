@@ -248,18 +248,27 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_volume2d(OpArgs
     u[c] = acc;
   }
   if (on && t < npc) pma = A.x[poff + (int64_t)a * L.Np + cell * npc + t];
-  // corners and geometry at quadrature point t
+  // corners and geometry at quadrature point t: read from the precomputed table for the Jacobian
+  // apply (the corners then only serve the boundary faces), else computed from the vertices
+  const bool bcell = on && (cc[0] == 0 || cc[1] == 0 || cc[0] == L.n - 1 || cc[1] == L.n - 1);
+  const bool use_geo = (MODE == MJ) && (A.geo != nullptr);
   T corner[4][3];
   {
+    const bool need = use_geo ? bcell : on;
     const int64_t v0 = (int64_t)cc[0] + (int64_t)(L.n + 1) * cc[1];
     const int64_t vv[4] = {v0, v0 + 1, v0 + L.n + 1, v0 + L.n + 2};
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int i = 0; i < 2; ++i) corner[q][i] = on ? L.verts[vv[q] * 2 + i] : (T)(((q >> i) & 1));
+      for (int i = 0; i < 2; ++i) corner[q][i] = need ? L.verts[vv[q] * 2 + i] : (T)(((q >> i) & 1));
   }
-  T G[3][3], xq[3], JxW;
-  {
+  T G[3][3], xq[3] = {0, 0, 0}, JxW;
+  if (use_geo) {
+    const T* gg = A.geo + cell * 5 * Q + t;
+    G[0][0] = on ? gg[0] : (T)1; G[0][1] = on ? gg[Q] : (T)0;
+    G[1][0] = on ? gg[2 * Q] : (T)0; G[1][1] = on ? gg[3 * Q] : (T)1;
+    JxW = on ? gg[4 * Q] : (T)0;
+  } else {
     T xh[3] = {tb.qx[tx], tb.qx[ty], 0}, J[3][3];
     map_jacobian<T, 2>(corner, xh, J, xq);
     JxW = invert<T, 2>(J, G) * tb.qw[tx] * tb.qw[ty];
@@ -280,7 +289,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_volume2d(OpArgs
     uq[c] = shfl_y<T, N>(v, sB, ty, cb + tx, false);
   }
   // cell volume |K| (for h_{Gamma_D} of boundary faces), needed only where a group has a face
-  const bool bcell = on && (cc[0] == 0 || cc[1] == 0 || cc[0] == L.n - 1 || cc[1] == L.n - 1);
   T vol = 0;
   if (MODE != MM && __any_sync(0xffffffffu, bcell)) {
 #pragma unroll
@@ -365,6 +373,31 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_volume2d(OpArgs
     for (int c = 0; c < 2; ++c) A.y[(int64_t)a * L.Nv + c * L.nnodes + gnode] += vout[c];
   }
   if (on && t < npc) A.y[poff + (int64_t)a * L.Np + cell * npc + t] += pacc;
+}
+
+// Geometry table of a 2D level for k_volume2d: per cell and Gauss point t the inverse Jacobian
+// G (dxhat_m/dx_l) and JxW of the multilinear map, computed exactly as in k_volume2d.
+template <typename T, int N>
+__global__ void k_geo2d(LevelArgs<T> L, Tab<T> tb, T* __restrict__ geo, int64_t ncells) {
+  constexpr int Q = N * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ncells * Q;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = e / Q;
+    const int t = (int)(e % Q), tx = t % N, ty = t / N;
+    const int cx = (int)(cell % L.n), cy = (int)(cell / L.n);
+    const int64_t v0 = (int64_t)cx + (int64_t)(L.n + 1) * cy;
+    const int64_t vv[4] = {v0, v0 + 1, v0 + L.n + 1, v0 + L.n + 2};
+    T corner[4][3];
+    for (int q = 0; q < 4; ++q) {
+      for (int i = 0; i < 2; ++i) corner[q][i] = L.verts[vv[q] * 2 + i];
+      corner[q][2] = 0;
+    }
+    T xh[3] = {tb.qx[tx], tb.qx[ty], 0}, J[3][3], G[3][3], xq[3];
+    map_jacobian<T, 2>(corner, xh, J, xq);
+    const T JxW = invert<T, 2>(J, G) * tb.qw[tx] * tb.qw[ty];
+    T* gg = geo + cell * 5 * Q + t;
+    gg[0] = G[0][0]; gg[Q] = G[0][1]; gg[2 * Q] = G[1][0]; gg[3 * Q] = G[1][1]; gg[4 * Q] = JxW;
+  }
 }
 
 }  // namespace stmg

@@ -98,6 +98,13 @@ static void build_level(Handle* h, Level& lv, const std::vector<double>& verts) 
     lv.bcells[c] = (int*)h->dalloc(bc.size() * sizeof(int));
     h->upload(lv.bcells[c], bc.data(), bc.size() * sizeof(int));
   }
+  if (lv.d == 2) {
+    // geometry table of the 2D Jacobian apply (5 values per cell and Gauss point, both precisions)
+    const size_t ng = (size_t)ncells * 5 * (lv.r + 2) * (lv.r + 2);
+    lv.geo64 = (double*)h->dalloc(ng * sizeof(double));
+    lv.geo32 = (float*)h->dalloc(ng * sizeof(float));
+    if (build_geometry(lv, h->pb, h->stream) != cudaSuccess) throw CudaFailure(cudaErrorLaunchFailure);
+  }
 }
 
 static std::vector<double> coarsen_vertices(const std::vector<double>& v, int d, int n) {
@@ -163,6 +170,7 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
     double Nv = d * nodes, Np = cells * npc;
     nst[l] = (lk + 1.0) * (Nv + Np);
     tot += 12.0 * std::pow(ln + 1.0, d) + 4.0 * cells;                  // vertices, boundary lists
+    if (d == 2) tot += cells * 5.0 * (lr + 2.0) * (lr + 2.0) * 12.0;    // 2D geometry tables
     tot += 5.0 * nst[l] * es;                                            // level vectors
     if (l + 1 < lv.size()) {
       double nl = std::pow(lr + 2.0, d), mv = d * nl, msp = mv + npc;
