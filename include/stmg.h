@@ -194,6 +194,15 @@ typedef struct {
  * rest of multigrid, other) during stmg_slab_solve (adds a few event records per phase). */
 stmg_status stmg_set_timing(stmg_handle* h, int on);
 
+/* Failure-handling test hook.  With on != 0, every following Vanka sweep of this handle outside
+ * a captured V-cycle arms the shared-memory barrier of its patch staging for 16 bytes more than
+ * it copies, so that the kernel's bounded wait runs out: the kernel flags the timeout, waits once
+ * more (also bounded) and leaves the correction of that cell unchanged; the call returns
+ * STMG_ERR_TIMEOUT.  No copy is left in flight and the GPU is not faulted, so the handle stays
+ * usable; on = 0 restores normal operation.  Each sweep launch takes up to a few seconds while
+ * the hook is on.  Not part of the method (no counterpart in the paper). */
+stmg_status stmg_test_wait_timeout(stmg_handle* h, int on);
+
 /* Restrict the per-kernel-class timers of stmg_set_timing to the classes whose bit is set in
  * mask (bit c = class c of stmg_kernel_profile; default: all).  Every timed launch adds two
  * event records (graph nodes inside the captured V-cycle), so timing one class perturbs the

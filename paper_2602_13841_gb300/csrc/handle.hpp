@@ -54,6 +54,7 @@ struct Handle {
   int* flag = nullptr;
   bool solver_ready = false;
   bool timing = false;
+  bool wait_fault = false;           // failure-test hook: Vanka applies wait for bytes never sent
   PhaseTimer t_rebuild, t_mg;
   // per kernel class (KernelClass) device time, launch count and algorithmic bytes, timing mode
   PhaseTimer kt[8];

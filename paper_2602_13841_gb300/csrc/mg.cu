@@ -169,7 +169,8 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
     h->kbegin(KC_VANKA_APPLY);
     if (l == 0) h->kbegin(KC_VANKA_APPLY0);
     for (int c = 0; c < lv.ncolors; ++c) {
-      CKE(vanka_apply<T>(lv, h->pb, inv[l], invh[l], iscale[l], res, d, omega, h->prm.omega_p, c, wstat, s));
+      CKE(vanka_apply<T>(lv, h->pb, inv[l], invh[l], iscale[l], res, d, omega, h->prm.omega_p, c, wstat, s,
+                         h->wait_fault ? 16u : 0u));
       cells += lv.colors[c].count;
     }
     if (l == 0) h->kend(KC_VANKA_APPLY0, (double)cells * (ib + 3.0 * m * sizeof(T)), lv.ncolors);

@@ -73,7 +73,8 @@ size_t vanka_work_entries(const Level& lv, size_t esize);  // global build works
 // inv: patch inverses of precision T, or (invh non-null) FP16 inverses scaled by scale[cell].
 template <typename T>
 cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
-                        const T* res, T* d, double omega, double omega_p, int color, int* wstat, cudaStream_t s);
+                        const T* res, T* d, double omega, double omega_p, int color, int* wstat, cudaStream_t s,
+                        unsigned extra_tx = 0);   // extra_tx: failure-test hook (see stmg_test_wait_timeout)
 size_t vanka_spatial_size(const Level& lv);          // m_s = d (r+2)^d + npc
 size_t vanka_patch_size(const Level& lv);            // m_st = (k+1) m_s
 size_t vanka_inv_entries(const Level& lv);           // stored reals of one cell's patch inverse ((k+1) m_s x stride)

@@ -469,6 +469,16 @@ stmg_status stmg_set_timing(stmg_handle* hh, int on) {
   return STMG_OK;
 }
 
+stmg_status stmg_test_wait_timeout(stmg_handle* hh, int on) {
+  if (!hh) return STMG_ERR_ARG;
+  Handle* h = H(hh);
+  h->wait_fault = on != 0;
+  // captured V-cycles bake the kernel arguments in
+  if (h->mg32) h->mg32->drop_graph();
+  if (h->mg64) h->mg64->drop_graph();
+  return STMG_OK;
+}
+
 stmg_status stmg_set_timing_classes(stmg_handle* hh, unsigned mask) {
   if (!hh) return STMG_ERR_ARG;
   H(hh)->kmask = mask;

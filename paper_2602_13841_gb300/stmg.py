@@ -82,6 +82,7 @@ def load():
         "stmg_level_state": (I, [P, I, V]),
         "stmg_set_timing": (I, [P, I]),
         "stmg_set_timing_classes": (I, [P, ctypes.c_uint]),
+        "stmg_test_wait_timeout": (I, [P, I]),
         "stmg_slab_solve": (I, [P, D, V, V, ctypes.POINTER(Stats)]),
         "stmg_kernel_profile": (I, [P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                     ctypes.POINTER(ctypes.c_double)]),
