@@ -79,6 +79,9 @@ typedef struct {
   int vanka_fp16;      /* 1: store the Vanka patch inverses as FP16 with one FP32 scale per patch
                           (half the smoother's memory traffic; the apply still accumulates in
                           the preconditioner precision).  0 (default): preconditioner precision. */
+  int build_chunk_cells; /* the smoother build computes the per-cell element matrices in chunks of
+                          whole cell planes of at most this many cells (at least three planes),
+                          bounding its scratch memory; <= 0 (default): 262144 */
 } stmg_params;
 
 /* Fill *p with the paper's defaults (Sec. 5, Alg. 1-2) for a d-dimensional problem. */

@@ -22,6 +22,7 @@ struct Level {
   int nbcells[8]{};
   int ncolors = 0;
   double hscale = 0;                  // Nitsche length factor (see LevelArgs)
+  int64_t chunk_cells = 262144;       // cells per chunk of the smoother build's element scratch
   double* geo64 = nullptr;            // 2D: geometry table of the Jacobian apply (see OpArgs::geo)
   float* geo32 = nullptr;
 };

@@ -36,9 +36,10 @@ cudaError_t MG<T>::allocate(Handle* hh) {
           inv[l] = (T*)h->dalloc((size_t)(lv.Np / lv.npc) * vanka_inv_entries(lv) * sizeof(T));
         }
         size_t nc = lv.Np / lv.npc;
-        ea = std::max(ea, nc * vanka_elem_size(lv, 0));
-        eb = std::max(eb, nc * vanka_elem_size(lv, 1));
-        em = std::max(em, nc * vanka_elem_size(lv, 2));
+        const size_t ec = vanka_elem_cells(lv);                 // element scratch: one chunk
+        ea = std::max(ea, ec * vanka_elem_size(lv, 0));
+        eb = std::max(eb, ec * vanka_elem_size(lv, 1));
+        em = std::max(em, ec * vanka_elem_size(lv, 2));
         nv = std::max(nv, (size_t)lv.Nv);
         wk = std::max(wk, vanka_work_entries(lv, sizeof(T)));
       }

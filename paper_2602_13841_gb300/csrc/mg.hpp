@@ -70,6 +70,7 @@ template <typename T>
 cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar, T* EA, T* EB, T* EM,
                         T* inv, void* invh, float* scale, int* status, T* work, cudaStream_t s);
 size_t vanka_work_entries(const Level& lv, size_t esize);  // global build workspace (0: on-chip patches)
+size_t vanka_elem_cells(const Level& lv);   // cells per chunk of the element-matrix scratch
 // inv: patch inverses of precision T, or (invh non-null) FP16 inverses scaled by scale[cell].
 template <typename T>
 cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,

@@ -142,6 +142,7 @@ void stmg_params_default(stmg_params* p) {
   p->stag_s = 3; p->stag_theta = 0.95;
   p->omega_p = 1.0;
   p->vanka_fp16 = 0;
+  p->build_chunk_cells = 0;
 }
 
 stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
@@ -177,7 +178,10 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
       const double st = std::ceil(msp / 8.0) * 8.0;                      // padded column stride
       const double ent = (lk + 1.0) * msp * st;                          // time-diagonalised inverse
       tot += p->vanka_fp16 ? cells * (ent * 2.0 + 4.0 * (lk + 1.0)) : cells * ent * es;  // patch inverses
-      ea = std::max(ea, cells * mv * mv); eb = std::max(eb, cells * npc * mv); em = std::max(em, cells * nl * nl);
+      // element-matrix scratch: chunks of cell planes, at most ~2^18 cells (three planes at least)
+      const double plane = cells / ln, cap = p->build_chunk_cells > 0 ? (double)p->build_chunk_cells : 262144.0;
+      const double ec = cells <= cap ? cells : std::min(cells, std::max(3.0, std::floor(cap / plane)) * plane);
+      ea = std::max(ea, ec * mv * mv); eb = std::max(eb, ec * npc * mv); em = std::max(em, ec * nl * nl);
       // patches beyond shared memory are factorised in a global workspace of 304 block slots
       const double pslot = 2.0 * msp * msp + mv * mv + nl * nl;
       if (es * (pslot + 2.0 * msp) + 4.0 * msp + 16.0 > 227.0 * 1024.0) wk = std::max(wk, 304.0 * pslot * es);
@@ -245,6 +249,7 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
     const double p0 = p->r + 1;
     for (auto& rk : pk) {
       Level lv; lv.d = d; lv.n = n; lv.r = rk.first; lv.k = rk.second;
+      if (p->build_chunk_cells > 0) lv.chunk_cells = p->build_chunk_cells;
       lv.hscale = 1.0 / (p0 * (p0 + 1.0));
       build_level(h.get(), lv, verts);
       h->levels.push_back(lv);
@@ -255,6 +260,7 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
       cv = coarsen_vertices(cv, d, nn);
       nn /= 2; ++hl;
       Level lv; lv.d = d; lv.n = nn; lv.r = r; lv.k = k;
+      if (p->build_chunk_cells > 0) lv.chunk_cells = p->build_chunk_cells;
       lv.hscale = ((double)nn / n) / (p0 * (p0 + 1.0));
       build_level(h.get(), lv, cv);
       h->levels.push_back(lv);

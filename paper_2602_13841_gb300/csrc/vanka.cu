@@ -71,6 +71,15 @@ static size_t work_slot(const Level& lv) {
   return 2 * ms * ms + mv * mv + nl * nl;
 }
 
+// Cells whose element matrices the build scratch holds at once (whole level if smaller).
+size_t vanka_elem_cells(const Level& lv) {
+  const size_t ncells = lv.Np / lv.npc, plane = ncells / lv.n;
+  const size_t cap = (size_t)lv.chunk_cells;
+  if (ncells <= cap) return ncells;
+  const size_t planes = cap / plane > 3 ? cap / plane : 3;     // a chunk plus its two halo planes
+  return planes * plane < ncells ? planes * plane : ncells;
+}
+
 size_t vanka_work_entries(const Level& lv, size_t es) {
   return patch_onchip(lv, es) ? 0 : (size_t)kWorkSlots * work_slot(lv);
 }
@@ -94,24 +103,41 @@ static cudaError_t build_dn(const Level& lv, const Problem& pb, const T* U, T* v
   k_midpoint<T><<<(int)g, 256, 0, s>>>(U, vstar, lv.Nv, lv.k + 1, tb);
   const bool onchip = patch_onchip(lv, sizeof(T));
   if (!onchip && !work) return cudaErrorInvalidValue;
-  VankaArgs<T> V{level_args<T>(lv, pb, 0.0), vstar, EA, EB, EM, inv, (__half*)invh, scale, status,
+  VankaArgs<T> V{level_args<T>(lv, pb, 0.0), vstar, EA, EB, EM, 0, inv, (__half*)invh, scale, status,
                  onchip ? nullptr : work, onchip ? 0 : (int64_t)work_slot(lv)};
   size_t es = elem_smem<D, N>(sizeof(T));
   cudaError_t e = allow_smem(k_elem<T, D, N>, es);
   if (e != cudaSuccess) return e;
-  k_elem<T, D, N><<<(unsigned)ncells, 256, es, s>>>(V, tb, ncells);
+  size_t ps = 0;
   if (onchip) {
-    size_t ps = patch_smem(lv, sizeof(T));
+    ps = patch_smem(lv, sizeof(T));
     e = allow_smem(k_patch<T, D, N>, ps);
     if (e != cudaSuccess) return e;
-    k_patch<T, D, N><<<(unsigned)ncells, 256, ps, s>>>(V, tb, make_teig<T>(lv.tabs, pb.tau), ncells);
   } else {
     const size_t ms = vanka_spatial_size(lv);
-    const size_t ps = sizeof(T) * 2 * ms + sizeof(int) * ms + 16;
-    const int64_t grid = ncells < kWorkSlots ? ncells : kWorkSlots;
-    k_patch_global<T, D, N><<<(unsigned)grid, 512, ps, s>>>(V, tb, make_teig<T>(lv.tabs, pb.tau), ncells);
+    ps = sizeof(T) * 2 * ms + sizeof(int) * ms + 16;
   }
-  note_launch(3);
+  const TEig<T> te = make_teig<T>(lv.tabs, pb.tau);
+  // chunks of whole cell planes (the last coordinate): the element matrices of the chunk and of
+  // one plane on either side (the patches' neighbours) fit the scratch of vanka_elem_cells cells
+  const int64_t plane = ncells / lv.n;
+  int64_t planes = (int64_t)vanka_elem_cells(lv) >= ncells ? lv.n : (int64_t)vanka_elem_cells(lv) / plane - 2;
+  if (planes < 1 || planes > lv.n) planes = lv.n;
+  for (int64_t z0 = 0; z0 < lv.n; z0 += planes) {
+    const int64_t z1 = z0 + planes < lv.n ? z0 + planes : lv.n;
+    const int64_t e0 = (z0 > 0 ? z0 - 1 : 0) * plane, e1 = (z1 < lv.n ? z1 + 1 : lv.n) * plane;
+    const int64_t p0 = z0 * plane, p1 = z1 * plane;
+    V.ebase = e0;
+    k_elem<T, D, N><<<(unsigned)(e1 - e0), 256, es, s>>>(V, tb, e0, e1);
+    if (onchip) {
+      k_patch<T, D, N><<<(unsigned)(p1 - p0), 256, ps, s>>>(V, tb, te, p0, p1);
+    } else {
+      const int64_t grid = p1 - p0 < kWorkSlots ? p1 - p0 : kWorkSlots;
+      k_patch_global<T, D, N><<<(unsigned)grid, 512, ps, s>>>(V, tb, te, p0, p1);
+    }
+    note_launch(2);
+  }
+  note_launch(1);
   return cudaGetLastError();
 }
 

@@ -26,9 +26,10 @@ template <typename T>
 struct VankaArgs {
   LevelArgs<T> L;
   const T* vstar;       // midpoint velocity field (Nv)
-  T* EA;                // [cells][mv][mv]
-  T* EB;                // [cells][npc][mv]
-  T* EM;                // [cells][nl][nl]
+  T* EA;                // [cells][mv][mv]   element matrices of the cells ebase, ebase+1, ...
+  T* EB;                // [cells][npc][mv]  (the build runs in chunks of cell planes that share
+  T* EM;                // [cells][nl][nl]    one scratch; cell c is stored at c - ebase)
+  int64_t ebase;
   // Patch inverse of a cell, time-diagonalised: one spatial inverse T_e^{-1} (size m_s = mv +
   // npc) per eigen-block e, column-major with padded stride inv_stride(m_s); a complex block
   // stores (re, im) pairs.  k+1 units of m_s x stride reals per cell, storage in T, or
@@ -74,7 +75,7 @@ __device__ inline void node_multi(int i, int* im) {
 
 // ---------------------------------------------------------------------------- element matrices
 template <typename T, int D, int N>
-__global__ void k_elem(VankaArgs<T> V, Tab<T> tb, int64_t ncells) {
+__global__ void k_elem(VankaArgs<T> V, Tab<T> tb, int64_t c0, int64_t c1) {
   constexpr int Q = Shape<D, N>::Q;
   constexpr int NL = Q;                  // local nodes per component (N = n_q)
   constexpr int NF = Shape<D, N>::NF;
@@ -93,8 +94,8 @@ __global__ void k_elem(VankaArgs<T> V, Tab<T> tb, int64_t ncells) {
   __shared__ int s_faces[6];
   __shared__ int s_nf;
 
-  const int64_t cell = blockIdx.x;
-  if (cell >= ncells) return;
+  const int64_t cell = c0 + blockIdx.x;
+  if (cell >= c1) return;
   const LevelArgs<T>& L = V.L;
   int cc[3] = {0, 0, 0};
   cell_coords<D>(cell, L.n, cc);
@@ -196,7 +197,7 @@ __global__ void k_elem(VankaArgs<T> V, Tab<T> tb, int64_t ncells) {
     __syncthreads();
   }
   // velocity block: entry (c, i ; e, j) = row (test c, i), column (trial e, j)
-  T* EA = V.EA + cell * (int64_t)MV * MV;
+  T* EA = V.EA + (cell - V.ebase) * (int64_t)MV * MV;
   for (int ent = tid; ent < MV * MV; ent += nt) {
     const int row = ent / MV, col = ent % MV;
     const int c = row / NL, i = row % NL, e = col / NL, j = col % NL;
@@ -236,7 +237,7 @@ __global__ void k_elem(VankaArgs<T> V, Tab<T> tb, int64_t ncells) {
   }
   // pressure x velocity block B_K[m][(e, j)]
   const int npc = tb.npc;
-  T* EB = V.EB + cell * (int64_t)npc * MV;
+  T* EB = V.EB + (cell - V.ebase) * (int64_t)npc * MV;
   for (int ent = tid; ent < npc * MV; ent += nt) {
     const int m = ent / MV, col = ent % MV, e = col / NL, j = col % NL;
     T acc = 0;
@@ -257,7 +258,7 @@ __global__ void k_elem(VankaArgs<T> V, Tab<T> tb, int64_t ncells) {
     }
     EB[ent] = acc;
   }
-  T* EM = V.EM + cell * (int64_t)NL * NL;
+  T* EM = V.EM + (cell - V.ebase) * (int64_t)NL * NL;
   for (int ent = tid; ent < NL * NL; ent += nt) {
     const int i = ent / NL, j = ent % NL;
     T acc = 0;
@@ -455,7 +456,7 @@ __device__ bool patch_cell(const VankaArgs<T>& V, const Tab<T>& tb, const TEig<T
         nc += (int64_t)x * s; s *= L.n;
         ii += a * si; jj += b * si; si *= N;
       }
-      if (ok) acc += V.EA[nc * (int64_t)MV * MV + (int64_t)(c * NL + ii) * MV + e * NL + jj];
+      if (ok) acc += V.EA[(nc - V.ebase) * (int64_t)MV * MV + (int64_t)(c * NL + ii) * MV + e * NL + jj];
     }
     Ap[ent] = acc;
   }
@@ -476,12 +477,12 @@ __device__ bool patch_cell(const VankaArgs<T>& V, const Tab<T>& tb, const TEig<T
         nc += (int64_t)x * s; s *= L.n;
         ii += a * si; jj += b * si; si *= N;
       }
-      if (ok) acc += V.EM[nc * (int64_t)NL * NL + (int64_t)ii * NL + jj];
+      if (ok) acc += V.EM[(nc - V.ebase) * (int64_t)NL * NL + (int64_t)ii * NL + jj];
     }
     Mp[ent] = acc;
   }
   __syncthreads();
-  const T* EB = V.EB + cell * (int64_t)npc * MV;
+  const T* EB = V.EB + (cell - V.ebase) * (int64_t)npc * MV;
   const int64_t cbase = cell * (int64_t)kp1 * ms * st;
   for (int e = 0; e < te.nblk; ++e) {
     const bool cplx = te.cplx[e] != 0;
@@ -539,7 +540,7 @@ __device__ bool patch_cell(const VankaArgs<T>& V, const Tab<T>& tb, const TEig<T
 
 // Patches whose matrices fit shared memory: one block per cell.
 template <typename T, int D, int N>
-__global__ void k_patch(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t ncells) {
+__global__ void k_patch(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t c0, int64_t c1) {
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int ms = MV + tb.npc;
@@ -551,8 +552,8 @@ __global__ void k_patch(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t ncells) {
   T* cr = Mp + NL * NL;                             // [ms]
   T* ci = cr + ms;                                  // [ms]
   int* piv = reinterpret_cast<int*>(ci + ms);       // [ms]
-  const int64_t cell = blockIdx.x;
-  if (cell >= ncells) return;
+  const int64_t cell = c0 + blockIdx.x;
+  if (cell >= c1) return;
   patch_cell<T, D, N>(V, tb, te, cell, Sr, Si, Ap, Mp, cr, ci, piv);
 }
 
@@ -560,7 +561,7 @@ __global__ void k_patch(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t ncells) {
 // (V.work, V.wslot entries per slot; the slots together stay L2-resident); blocks stride over
 // the cells.  Only the pivot bookkeeping is in shared memory.
 template <typename T, int D, int N>
-__global__ void k_patch_global(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t ncells) {
+__global__ void k_patch_global(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t c0, int64_t c1) {
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int ms = MV + tb.npc;
@@ -572,7 +573,7 @@ __global__ void k_patch_global(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t nc
   T* Si = Sr + ms * ms;
   T* Ap = Si + ms * ms;
   T* Mp = Ap + MV * MV;
-  for (int64_t cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
+  for (int64_t cell = c0 + blockIdx.x; cell < c1; cell += gridDim.x) {
     if (!patch_cell<T, D, N>(V, tb, te, cell, Sr, Si, Ap, Mp, cr, ci, piv)) return;
     __syncthreads();
   }

@@ -38,7 +38,7 @@ class Params(ctypes.Structure):
         ("rebuild_thetaN", ctypes.c_double), ("rebuild_thetaL", ctypes.c_double),
         ("rebuild_kappa_abs", ctypes.c_int),
         ("stag_s", ctypes.c_int), ("stag_theta", ctypes.c_double),
-        ("omega_p", ctypes.c_double), ("vanka_fp16", ctypes.c_int),
+        ("omega_p", ctypes.c_double), ("vanka_fp16", ctypes.c_int), ("build_chunk_cells", ctypes.c_int),
     ]
 
 

@@ -190,3 +190,28 @@ def test_slab_solve_with_fp16_patch_inverses(precision):
     got = _np(U)
     assert _rel(got[:nv], Ud[:nv]) < 1e-7
     assert np.abs(got[nv:] - Ud[nv:]).max() < 1e-6 * max(np.abs(Ud[nv:]).max(), 1.0)
+
+
+@pytest.mark.parametrize("d,n,r,k,prec", [(2, 16, 2, 2, "fp32"), (3, 8, 1, 1, "fp64")])
+def test_chunked_smoother_build_equals_single_chunk(d, n, r, k, prec):
+    """The smoother build in chunks of cell planes (element matrices of a chunk plus one halo
+    plane on either side) gives the same patch inverses, hence bit-identical sweeps, as one
+    chunk over the whole level."""
+    import torch
+    from paper_2602_13841_gb300 import stmg
+    build_and_load()
+    verts = inputs.vertices(d, n, 0.1, 4)
+    p0 = stmg.STMG_FP64 if prec == "fp64" else stmg.STMG_FP32
+    out = []
+    for chunk in (0, 2 * n ** (d - 1)):          # default (one chunk) / two planes per chunk
+        p = stmg.default_params(dim=d, n_cells_1d=n, r=r, k=k, nu=1e-2, tau=0.05, problem="TG2D" if d == 2 else "TG3D",
+                                precond_precision=p0, build_chunk_cells=chunk)
+        S = stmg.Solver(p, verts)
+        L = S.levels[0]
+        S.smoother_build(_t(inputs.uniform(L["Nst"], 8)))
+        got = _t(inputs.uniform(L["Nst"], 9), S.pdtype)
+        S.smoother_sweep(0, _t(inputs.uniform(L["Nst"], 10), S.pdtype), got, 2, zero_start=False)
+        torch.cuda.synchronize()
+        out.append(got.cpu())
+        S.close()
+    assert torch.equal(out[0], out[1])
