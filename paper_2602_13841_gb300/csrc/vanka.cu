@@ -52,7 +52,7 @@ static bool patch_onchip(const Level& lv, size_t es) { return patch_smem(lv, es)
 
 // The stored inverse blob of a cell fits shared memory (else k_vanka_apply_global).
 static bool apply_onchip(const Level& lv, size_t es_store, size_t es) {
-  return apply_smem_bytes(lv.k + 1, (int)vanka_spatial_size(lv), es_store, es) <= 227 * 1024;
+  return apply_slot_bytes(lv.k + 1, (int)vanka_spatial_size(lv), es_store, es) <= 227 * 1024;
 }
 
 bool vanka_supported(const Level& lv, size_t es) {
@@ -168,10 +168,15 @@ static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv
         make_teig<T>(lv.tabs, pb.tau), ci);
     return cudaSuccess;
   }
-  const size_t smem = apply_smem_bytes(kp1, ms, sizeof(SI), sizeof(T));
+  // cells per block: 4 for one-warp patches, 2 for two-warp patches (32 resident blocks per SM)
+  const size_t slot = apply_slot_bytes(kp1, ms, sizeof(SI), sizeof(T));
+  int cpb = threads <= 32 ? 4 : threads <= 64 ? 2 : 1;
+  while (cpb > 1 && (size_t)cpb * slot > 100 * 1024) cpb /= 2;
+  const size_t smem = (size_t)cpb * slot;
   cudaError_t e = allow_smem(k_vanka_apply<T, SI, D, N>, smem);
   if (e != cudaSuccess) return e;
-  k_vanka_apply<T, SI, D, N><<<(unsigned)ci.count, threads, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, scale, res, d,
+  const unsigned blocks = (unsigned)((ci.count + cpb - 1) / cpb);
+  k_vanka_apply<T, SI, D, N><<<blocks, threads * cpb, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, scale, res, d,
                                                                        (T)omega, (T)omega_p, kp1, lv.npc,
                                                                        make_teig<T>(lv.tabs, pb.tau), ci, wstat, extra_tx);
   return cudaSuccess;

@@ -648,6 +648,10 @@ __host__ __device__ inline size_t apply_smem_bytes(int kp1, int ms, size_t si, s
   const int mr = (ms + 1) & ~1;
   return apply_blob_bytes(kp1, ms, si) + (((size_t)kp1 * mr * t + 7) & ~(size_t)7) + (size_t)ms * 8 + 16;
 }
+// One cell's slot of a multi-cell block, rounded so that every slot's blob starts 128-byte aligned.
+__host__ __device__ inline size_t apply_slot_bytes(int kp1, int ms, size_t si, size_t t) {
+  return (apply_smem_bytes(kp1, ms, si, t) + 127) & ~(size_t)127;
+}
 
 template <typename T, typename SI, int D, int N>
 __global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const float* __restrict__ scale,
@@ -656,33 +660,40 @@ __global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const 
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int ms = MV + npc, st = inv_stride(ms), mr = (ms + 1) & ~1;
+  // small patches: several cells per block (slots of tpc threads), so that more cells are in
+  // flight than the 32-blocks-per-SM limit would allow with one-warp blocks
+  const int tpc = ((ms + 31) / 32) * 32, slot = threadIdx.x / tpc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + (size_t)slot * apply_slot_bytes(kp1, ms, sizeof(SI), sizeof(T));
   const size_t blob = apply_blob_bytes(kp1, ms, sizeof(SI));
-  SI* sinv = reinterpret_cast<SI*>(smem_raw);
-  T* rt = reinterpret_cast<T*>(smem_raw + blob);                                      // [kp1 units][mr]
-  int64_t* gb = reinterpret_cast<int64_t*>(smem_raw + blob + (((size_t)kp1 * mr * sizeof(T) + 7) & ~(size_t)7));
+  SI* sinv = reinterpret_cast<SI*>(base);
+  T* rt = reinterpret_cast<T*>(base + blob);                                          // [kp1 units][mr]
+  int64_t* gb = reinterpret_cast<int64_t*>(base + blob + (((size_t)kp1 * mr * sizeof(T) + 7) & ~(size_t)7));
   uint64_t* bar = reinterpret_cast<uint64_t*>(gb + ms);
-  const int cidx = blockIdx.x;
-  if (cidx >= ci.count) return;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int cidx = blockIdx.x * (blockDim.x / tpc) + slot;
+  const bool active = cidx < ci.count;
+  const int tid = threadIdx.x - slot * tpc, nt = tpc;
   int cc[3] = {0, 0, 0};
-  decode_color_cell<D>(ci, cidx, cc);
-  int64_t cell = 0, s = 1;
-  for (int l = 0; l < D; ++l) { cell += (int64_t)cc[l] * s; s *= L.n; }
-  // stage the cell's inverse: one thread arms the barrier and issues the bulk copies
+  int64_t cell = 0;
+  if (active) {
+    decode_color_cell<D>(ci, cidx, cc);
+    int64_t s = 1;
+    for (int l = 0; l < D; ++l) { cell += (int64_t)cc[l] * s; s *= L.n; }
+  }
+  // stage the cell's inverse: one thread per slot arms the barrier and issues the bulk copies
   const uint32_t b = smem_addr(bar);
   const uint32_t bytes = (uint32_t)((size_t)kp1 * ms * st * sizeof(SI));
-  if (tid == 0) {
+  if (active && tid == 0) {
     mbar_init(b, 1);
     mbar_expect_tx(b, bytes + extra_tx);            // extra_tx > 0 only under the failure-test hook
     const unsigned char* src = reinterpret_cast<const unsigned char*>(inv + cell * (int64_t)kp1 * ms * st);
     for (uint32_t o = 0; o < bytes; o += kBulkChunk) {
       const uint32_t n = bytes - o < (uint32_t)kBulkChunk ? bytes - o : (uint32_t)kBulkChunk;
-      bulk_g2s(smem_addr(smem_raw + o), src + o, n, b);
+      bulk_g2s(smem_addr(base + o), src + o, n, b);
     }
   }
   // meanwhile: gather the residual on the patch and transform it to the time eigenbasis
-  for (int l = tid; l < ms; l += nt) {
+  for (int l = tid; active && l < ms; l += nt) {
     int64_t g, sa;
     if (l < MV) {
       const int c = l / NL, i = l % NL;
@@ -704,10 +715,11 @@ __global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const 
       if (te.cplx[e]) rt[(te.off[e] + 1) * mr + l] = fi;
     }
   }
-  __syncthreads();                                   // barrier initialised, rt and gb complete
+  __syncthreads();                                   // barriers initialised, rt and gb complete
+  if (!active) return;
   if (!mbar_wait_bounded(b, 0, kWaitLimit)) {
     // the copy did not complete in time: report, give it a second bounded wait (it writes this
-    // block's shared memory) and leave d unchanged for this cell
+    // slot's shared memory) and leave d unchanged for this cell
     if (tid == 0) atomicExch(wstat, 1);
     mbar_wait_bounded(b, 0, kWaitLimit);
     return;
