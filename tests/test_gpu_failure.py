@@ -13,11 +13,11 @@ from tests.helpers import build_and_load, have_gpu
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not have_gpu(), reason="needs a CUDA GPU")]
 
 
-def _handle():
+def _handle(r):
     import torch
     from paper_2602_13841_gb300 import inputs, stmg
     build_and_load()
-    p = stmg.default_params(dim=2, n_cells_1d=4, r=1, k=1, nu=1e-2, tau=0.05, problem="TG2D",
+    p = stmg.default_params(dim=2, n_cells_1d=4, r=r, k=1, nu=1e-2, tau=0.05, problem="TG2D",
                             precond_precision=stmg.STMG_FP32)
     S = stmg.Solver(p, inputs.vertices(2, 4, 0.1, 3))
     L = S.levels[0]
@@ -25,10 +25,11 @@ def _handle():
     return S
 
 
-def test_vanka_wait_timeout_is_reported_and_the_handle_recovers():
+@pytest.mark.parametrize("r", [1, 2])     # one-warp patches (4 cells per block) / persistent pipeline
+def test_vanka_wait_timeout_is_reported_and_the_handle_recovers(r):
     import torch
     from paper_2602_13841_gb300 import inputs, stmg
-    S = _handle()
+    S = _handle(r)
     L = S.levels[0]
     rhs = torch.tensor(inputs.uniform(L["Nst"], 11), dtype=torch.float32, device="cuda")
     d0 = torch.tensor(inputs.uniform(L["Nst"], 12), dtype=torch.float32, device="cuda")
@@ -41,7 +42,7 @@ def test_vanka_wait_timeout_is_reported_and_the_handle_recovers():
     assert lib.stmg_test_wait_timeout(S.h, 0) == 0
     d = d0.clone()
     S.smoother_sweep(0, rhs, d, 1, zero_start=False)
-    ref = _handle()
+    ref = _handle(r)
     d_ref = d0.clone()
     ref.smoother_sweep(0, rhs, d_ref, 1, zero_start=False)
     torch.cuda.synchronize()
