@@ -168,26 +168,8 @@ static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv
         make_teig<T>(lv.tabs, pb.tau), ci);
     return cudaSuccess;
   }
-  const size_t slot = apply_slot_bytes(kp1, ms, sizeof(SI), sizeof(T));
-  if (threads > 32 && 2 * slot <= 64 * 1024) {
-    // persistent double-buffered blocks, as many as are resident at once
-    const size_t smem2 = 2 * slot;
-    cudaError_t e = allow_smem(k_vanka_apply_pipe<T, SI, D, N>, smem2);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vanka_apply_pipe<T, SI, D, N>, threads, smem2);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t resident = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 152);
-    const unsigned blocks = (unsigned)(ci.count < resident ? ci.count : resident);
-    k_vanka_apply_pipe<T, SI, D, N><<<blocks, threads, smem2, s>>>(level_args<T>(lv, pb, 0.0), inv, scale, res, d,
-                                                                  (T)omega, (T)omega_p, kp1, lv.npc,
-                                                                  make_teig<T>(lv.tabs, pb.tau), ci, wstat, extra_tx);
-    return cudaSuccess;
-  }
   // cells per block: 4 for one-warp patches (32 resident blocks per SM), else 1
+  const size_t slot = apply_slot_bytes(kp1, ms, sizeof(SI), sizeof(T));
   int cpb = threads <= 32 ? 4 : 1;
   while (cpb > 1 && (size_t)cpb * slot > 100 * 1024) cpb /= 2;
   const size_t smem = (size_t)cpb * slot;

@@ -761,130 +761,6 @@ __global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const 
   }
 }
 
-// Persistent, double-buffered variant of k_vanka_apply for two-warp patches: a block walks its
-// cells (blockIdx.x, + gridDim.x, ...) and, while it gathers, solves and scatters one cell, the
-// bulk copy of its next cell's inverse is already in flight into the other buffer.  Same
-// arithmetic and results as k_vanka_apply.
-template <typename T, typename SI, int D, int N>
-__global__ void k_vanka_apply_pipe(LevelArgs<T> L, const SI* __restrict__ inv, const float* __restrict__ scale,
-                                   const T* __restrict__ res, T* __restrict__ d, T omega, T omega_p, int kp1,
-                                   int npc, TEig<T> te, ColorInfo ci, int* __restrict__ wstat, unsigned extra_tx) {
-  constexpr int NL = Shape<D, N>::Q;
-  constexpr int MV = D * NL;
-  const int ms = MV + npc, st = inv_stride(ms), mr = (ms + 1) & ~1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const size_t slot = apply_slot_bytes(kp1, ms, sizeof(SI), sizeof(T));
-  const size_t blob = apply_blob_bytes(kp1, ms, sizeof(SI));
-  const size_t rtb = ((size_t)kp1 * mr * sizeof(T) + 7) & ~(size_t)7;
-  const uint32_t bytes = (uint32_t)((size_t)kp1 * ms * st * sizeof(SI));
-  const int tid = threadIdx.x, nt = blockDim.x;
-  int64_t c = blockIdx.x;
-  if (c >= ci.count) return;
-  auto bar_of = [&](int b) { return smem_addr(smem_raw + b * slot + blob + rtb + (size_t)ms * 8); };
-  auto cell_of = [&](int64_t cidx, int* cc) {
-    decode_color_cell<D>(ci, (int)cidx, cc);
-    int64_t cell = 0, s = 1;
-    for (int l = 0; l < D; ++l) { cell += (int64_t)cc[l] * s; s *= L.n; }
-    return cell;
-  };
-  auto issue = [&](int b, int64_t cidx) {            // thread 0 only
-    int cc[3] = {0, 0, 0};
-    const int64_t cell = cell_of(cidx, cc);
-    mbar_expect_tx(bar_of(b), bytes + extra_tx);     // extra_tx > 0 only under the failure-test hook
-    const unsigned char* src = reinterpret_cast<const unsigned char*>(inv + cell * (int64_t)kp1 * ms * st);
-    for (uint32_t o = 0; o < bytes; o += kBulkChunk) {
-      const uint32_t n = bytes - o < (uint32_t)kBulkChunk ? bytes - o : (uint32_t)kBulkChunk;
-      bulk_g2s(smem_addr(smem_raw + b * slot + o), src + o, n, bar_of(b));
-    }
-  };
-  if (tid == 0) {
-    mbar_init(bar_of(0), 1);
-    mbar_init(bar_of(1), 1);
-    issue(0, c);
-  }
-  __syncthreads();                                     // barriers initialised before any wait
-  for (int it = 0; c < ci.count; ++it, c += gridDim.x) {
-    const int b = it & 1;
-    const int64_t cn = c + gridDim.x;
-    if (cn < ci.count && tid == 0) issue(b ^ 1, cn);  // buffer b^1 was released at the end of it-1
-    SI* sinv = reinterpret_cast<SI*>(smem_raw + b * slot);
-    T* rt = reinterpret_cast<T*>(smem_raw + b * slot + blob);
-    int64_t* gb = reinterpret_cast<int64_t*>(smem_raw + b * slot + blob + rtb);
-    int cc[3] = {0, 0, 0};
-    const int64_t cell = cell_of(c, cc);
-    for (int l = tid; l < ms; l += nt) {
-      int64_t g, sa;
-      if (l < MV) {
-        const int cp = l / NL, i = l % NL;
-        g = cp * L.nnodes + global_node<D>(L.N1, cc, N - 1, i, N);
-        sa = L.Nv;
-      } else {
-        g = (int64_t)kp1 * L.Nv + cell * npc + (l - MV);
-        sa = L.Np;
-      }
-      gb[l] = g;
-      T ra[MAXKP1];
-#pragma unroll
-      for (int a = 0; a < MAXKP1; ++a) ra[a] = a < kp1 ? res[g + a * sa] : (T)0;
-      for (int e = 0; e < te.nblk; ++e) {
-        T fr = 0, fi = 0;
-#pragma unroll
-        for (int a = 0; a < MAXKP1; ++a) { fr += te.Fre[e][a] * ra[a]; fi += te.Fim[e][a] * ra[a]; }
-        rt[te.off[e] * mr + l] = fr;
-        if (te.cplx[e]) rt[(te.off[e] + 1) * mr + l] = fi;
-      }
-    }
-    const bool ok = mbar_wait_bounded(bar_of(b), (uint32_t)((it >> 1) & 1), kWaitLimit);
-    if (__syncthreads_or(!ok)) {
-      // a copy did not complete in time (block-uniform decision): report, give the copies still
-      // in flight into this block's buffers a second bounded wait, leave the remaining cells alone
-      if (tid == 0) {
-        atomicExch(wstat, 1);
-        mbar_wait_bounded(bar_of(b), (uint32_t)((it >> 1) & 1), kWaitLimit);
-        if (cn < ci.count) mbar_wait_bounded(bar_of(b ^ 1), (uint32_t)(((it + 1) >> 1) & 1), kWaitLimit);
-      }
-      return;
-    }
-    const int i = tid;
-    if (i < ms) {
-      T yr[MAXKP1], yi[MAXKP1];
-#pragma unroll
-      for (int e = 0; e < MAXKP1; ++e) { yr[e] = 0; yi[e] = 0; }
-      for (int e = 0; e < te.nblk; ++e) {
-        const SI* blk = sinv + (int64_t)te.off[e] * ms * st;
-        const T* r0 = rt + te.off[e] * mr;
-        T ar = 0, ai = 0;
-        if (!te.cplx[e]) {
-          for (int j = 0; j < ms; ++j) ar += (T)InvLd<SI>::re(blk + j * st + i) * r0[j];
-        } else {
-          const T* r1 = r0 + mr;
-          for (int j = 0; j < ms; ++j) {
-            const auto v = InvLd<SI>::cx(blk + 2 * (j * st + i));
-            const T vr = (T)v.x, vi = (T)v.y, xr = r0[j], xi = r1[j];
-            ar += vr * xr - vi * xi;
-            ai += vr * xi + vi * xr;
-          }
-        }
-        const T sc = scale ? (T)scale[cell * te.nblk + e] : (T)1;
-#pragma unroll
-        for (int q = 0; q < MAXKP1; ++q)
-          if (q == e) { yr[q] = sc * ar; yi[q] = sc * ai; }
-      }
-      const int64_t g = gb[i];
-      const int64_t sa = i < MV ? L.Nv : L.Np;
-      const T wgt = i < MV ? omega : omega_p;
-      for (int a = 0; a < kp1; ++a) {
-        T y = 0;
-#pragma unroll
-        for (int e = 0; e < MAXKP1; ++e)
-          if (e < te.nblk) y += te.Gre[a][e] * yr[e] - te.Gim[a][e] * yi[e];
-        d[g + a * sa] += wgt * y;
-      }
-    }
-    __syncthreads();                                   // buffer b is free for the copy after next
-  }
-}
-
 // Patches whose inverse blob exceeds shared memory (3D, r >= 2): the same arithmetic as
 // k_vanka_apply, each thread streaming its row of every block straight from global memory.
 template <typename SI> struct InvLdG;

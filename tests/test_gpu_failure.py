@@ -25,7 +25,7 @@ def _handle(r):
     return S
 
 
-@pytest.mark.parametrize("r", [1, 2])     # one-warp patches (4 cells per block) / persistent pipeline
+@pytest.mark.parametrize("r", [1, 2])     # one-warp patches (4 cells per block) / one cell per block
 def test_vanka_wait_timeout_is_reported_and_the_handle_recovers(r):
     import torch
     from paper_2602_13841_gb300 import inputs, stmg
