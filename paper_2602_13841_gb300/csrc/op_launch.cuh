@@ -51,7 +51,9 @@ static cudaError_t launch_dn(const Level& lv, const Problem& pb, double t0, cons
   while (smem > 160 * 1024 && cpb > 1) { --cpb; smem = cpb * vol_smem_per_cell<T, D, N, MODE>(kp1); }
   cudaError_t e = allow_smem(k_volume<T, D, N, MODE>, (size_t)smem);
   if (e != cudaSuccess) return e;
-  int fcpb = 256 / Q; if (fcpb < 1) fcpb = 1;
+  // faces: one boundary cell per block, so that the loop over the six faces skips the faces the
+  // cell does not have (a block of several cells runs every face any of them has)
+  int fcpb = 1;
   int fsmem = fcpb * face_smem_per_cell<T, D, N>(kp1);
   while (fsmem > 160 * 1024 && fcpb > 1) { --fcpb; fsmem = fcpb * face_smem_per_cell<T, D, N>(kp1); }
   if (MODE != MM) {

@@ -73,6 +73,19 @@ struct OpArgs {
                      // JxW at the quadrature points (precomputed at set-up), or null
 };
 
+// The reference tables are kernel parameters; indexing them with lane-dependent indices (a
+// quadrature point, a node) serialises the constant-bank reads, so the 3D kernels copy them to
+// shared memory first and read them from there.
+template <typename T>
+__device__ __forceinline__ const Tab<T>& stage_tab(const Tab<T>& tb_param, unsigned char* s_raw) {
+  static_assert(sizeof(Tab<T>) % 4 == 0, "Tab is copied in 4-byte words");
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&tb_param);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(s_raw);
+  for (int w = threadIdx.x; w < (int)(sizeof(Tab<T>) / 4); w += blockDim.x) dst[w] = src[w];
+  __syncthreads();
+  return *reinterpret_cast<const Tab<T>*>(s_raw);
+}
+
 template <int D>
 __device__ inline int64_t global_node(int N1, const int* cc, int r1, int t, int N) {
   int64_t g = 0, stride = 1;
@@ -98,7 +111,9 @@ __device__ inline void load_corners(const LevelArgs<T>& L, const int* cc, T (*co
 enum { MJ = 0, MR = 1, MM = 2 };   // Jacobian apply, residual, mass (w_a M_h, w_a M_p)
 
 template <typename T, int D, int N, int MODE>
-__global__ void k_volume(OpArgs<T> A, Tab<T> tb, ColorInfo ci, int cpb) {
+__global__ void k_volume(OpArgs<T> A, Tab<T> tb_p, ColorInfo ci, int cpb) {
+  __shared__ __align__(16) unsigned char s_tab[sizeof(Tab<T>)];
+  const Tab<T>& tb = stage_tab(tb_p, s_tab);
   constexpr bool RES = (MODE == MR);
   constexpr bool MASS = (MODE == MM);
   constexpr int Q = Shape<D, N>::Q;
@@ -308,7 +323,9 @@ __device__ inline T face_psi(const Tab<T>& tb, int axis, int side, const int* pq
 }
 
 template <typename T, int D, int N, int MODE>
-__global__ void k_faces(OpArgs<T> A, Tab<T> tb, const int* __restrict__ bcells, int nb, int cpb) {
+__global__ void k_faces(OpArgs<T> A, Tab<T> tb_p, const int* __restrict__ bcells, int nb, int cpb) {
+  __shared__ __align__(16) unsigned char s_tab[sizeof(Tab<T>)];
+  const Tab<T>& tb = stage_tab(tb_p, s_tab);
   constexpr int Q = Shape<D, N>::Q;
   constexpr int NF = Shape<D, N>::NF;
   const int kp1 = tb.k + 1, npc = tb.npc;
@@ -372,6 +389,7 @@ __global__ void k_faces(OpArgs<T> A, Tab<T> tb, const int* __restrict__ bcells, 
       // uniform across the block: every group runs the loop; groups whose cell does not have
       // this boundary face stay idle (flag `has`)
       const bool has = on && (side == 0 ? cc[axis] == 0 : cc[axis] == L.n - 1);
+      if (!__syncthreads_or(has)) continue;            // no cell of the block has this face
       int pq[2] = {t % N, t / N};
       T nrm[3] = {0, 0, 0}, ghat[3] = {0, 0, 0}, G[3][3], JxWf = 0, xf[3] = {0, 0, 0};
       if (has && t < NF) {
