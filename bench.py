@@ -9,7 +9,7 @@ One step = one slab solve (residual, Jacobian applies, smoother rebuilds, V-cycl
 Newton with Armijo): the whole hot path.  K steps march K consecutive slabs from t = 0
 (K = 4 is the full 4-slab configuration).  value = space-time DoFs solved per second
 (sum of N_st over the K slabs / device time).  Inputs are resident in HBM when the timed
-region starts; the working set (Vanka patch inverses, 3.4 GB) exceeds the L2 cache.
+region starts; the working set (the finest level's patch inverses alone 1.2 GB) exceeds the L2 cache.
 e2e: the same solves through the C ABI with the step's input (V_prev) copied from pinned host
 memory and the result (U) copied back inside the timed region.
 
@@ -43,6 +43,16 @@ ATOL = 1e-14
 # Smoother of both arms: omega = 1.2 / 2^d (library default), pressure relaxation 1, five pre-
 # and five post-sweeps per level (the lowest time to the Newton tolerance on this workload).
 SMOOTH = dict(nu1=5, nu2=5, omega_p=1.0)
+# Other workloads (`--workload`, profiling and scaling runs; the headline is "2d"):
+#   3d: 3D unit cube 128^3 mapped, Q2/P1disc (r=1), DG(2), dt=0.01, Re=400 manufactured solution,
+#       FGMRES restart 30, one pre- and post-sweep, FP16 patch storage from 96^3 cells (memory).
+WORKLOADS = {
+    "2d": dict(WORKLOAD, name=WORKLOAD_NAME, smooth=5, restart=50, oracle_n=8),
+    "3d": dict(d=3, n=128, r=1, k=2, amp=0.1, seed=1234, nu=1.0 / 400, tau=0.01, problem="MMS3D",
+               name=("3D unit cube 128^3 mapped (amp 0.1h, seed 1234), Q2/P1disc (r=1), DG(2), dt=0.01, "
+                     "Re=400 manufactured solution; FP32 hp-STMG in FP64 Newton-FGMRES (restart 30)"),
+               smooth=1, restart=30, oracle_n=2),
+}
 
 
 def _dist():
@@ -104,12 +114,12 @@ def _cpu_cores():
         return os.cpu_count() or 1
 
 
-def oracle_sample(n=16, slabs=1, smooth=SMOOTH["nu1"]):
+def oracle_sample(n=16, slabs=1, smooth=SMOOTH["nu1"], w=None):
     """FP64 CPU oracle slab solves on a bounded sample: the workload's (d, r, k, dt, Re, mesh
     recipe) on an n x n mesh.  Returns (DoF/s, seconds, N_st, description)."""
     from oracle import forms, krylov, problems
     from paper_2602_13841_gb300 import inputs
-    w = WORKLOAD
+    w = w or WORKLOAD
     prob = problems.make(w["problem"], w["nu"])
     verts = inputs.vertices(w["d"], n, w["amp"], w["seed"])
     S = krylov.SlabSolver(w["d"], n, w["r"], w["k"], verts, w["tau"], prob, rtol=1e-10, atol=ATOL,
@@ -122,8 +132,8 @@ def oracle_sample(n=16, slabs=1, smooth=SMOOTH["nu1"]):
         X, st = S.solve(U0, Vprev, sl * w["tau"])
         Vprev = L.lay.v(X, w["k"]).copy()
     dt = time.perf_counter() - t
-    desc = ("oracle Newton-FGMRES-hpSTMG slab solve, %dx%d mesh of the same recipe, r=%d, k=%d, %d slab(s), "
-            "N_st=%d" % (n, n, w["r"], w["k"], slabs, L.Nst))
+    desc = ("oracle Newton-FGMRES-hpSTMG slab solve, %d^%d mesh of the same recipe, r=%d, k=%d, %d slab(s), "
+            "N_st=%d" % (n, w["d"], w["r"], w["k"], slabs, L.Nst))
     return L.Nst * slabs / dt, dt, L.Nst, desc
 
 
@@ -131,19 +141,20 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
+    W = WORKLOADS[args.workload]
     for _ in range(args.warmup):
-        oracle_sample(n=4, smooth=args.smooth)
+        oracle_sample(n=min(4, W["oracle_n"]), smooth=args.smooth, w=W)
     vals = []
     t_tot = 0.0
     for _ in range(args.steps):
-        v, dt, nst, desc = oracle_sample(n=args.ref_n, smooth=args.smooth)
+        v, dt, nst, desc = oracle_sample(n=args.ref_n or W["oracle_n"], smooth=args.smooth, w=W)
         vals.append(v)
         t_tot += dt
     value = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "sample": desc},
+            "data": "synthetic", "config": {"workload": W["name"], "sample": desc},
             "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": _cpu_cores(), "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -156,15 +167,24 @@ def main():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-n", type=int, default=8)
+    ap.add_argument("--ref-n", type=int, default=0, help="oracle sample mesh (0: the workload's)")
+    ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS), help="2d: the headline configuration")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="cells per direction (profiling runs only)")
-    ap.add_argument("--vanka-fp16", type=int, default=0, help="1: FP16 storage of the patch inverses")
-    ap.add_argument("--smooth", type=int, default=SMOOTH["nu1"], help="Vanka pre- and post-sweeps per level")
+    ap.add_argument("--n", type=int, default=0, help="cells per direction (0: the workload's; profiling runs)")
+    ap.add_argument("--vanka-fp16", type=int, default=-1, help="1: FP16 storage of the patch inverses "
+                                                                   "(-1: the workload's choice)")
+    ap.add_argument("--smooth", type=int, default=0, help="Vanka pre- and post-sweeps per level (0: the workload's)")
     ap.add_argument("--serving-requests", type=int, default=16,
                     help="requests of the serving leg (Poisson stream, 20/s); 0 skips it")
     args = ap.parse_args()
+    W = WORKLOADS[args.workload]
+    if args.n <= 0:
+        args.n = W["n"]
+    if args.smooth <= 0:
+        args.smooth = W["smooth"]
+    if args.vanka_fp16 < 0:
+        args.vanka_fp16 = 1 if (W["d"] == 3 and args.n >= 96) else 0
     if args.impl == "reference":
         return run_reference(args)
 
@@ -179,11 +199,12 @@ def main():
 
     from paper_2602_13841_gb300 import build, inputs, stmg
     build.build()
-    w = dict(WORKLOAD)
+    w = dict(W)
     w["n"] = args.n
     p = stmg.default_params(dim=w["d"], n_cells_1d=w["n"], r=w["r"], k=w["k"], nu=w["nu"], tau=w["tau"],
                             problem=w["problem"], precond_precision=stmg.STMG_FP32, newton_rtol=1e-10,
                             newton_atol=ATOL, vanka_fp16=int(args.vanka_fp16),
+                            gmres_restart=w["restart"], gmres_maxit=w["restart"],
                             **dict(SMOOTH, nu1=args.smooth, nu2=args.smooth))
     stream = torch.cuda.Stream(device=dev)
     S = stmg.Solver(p, inputs.vertices(w["d"], w["n"], w["amp"], w["seed"]), stream=stream.cuda_stream)
@@ -293,16 +314,17 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            v, dt, nst, desc = oracle_sample(n=8, smooth=args.smooth)
+            v, dt, nst, desc = oracle_sample(n=W["oracle_n"], smooth=args.smooth, w=W)
             cpu = {"value": v, "unit": "DoF/s", "cores": _cpu_cores(), "kind": "oracle", "sample": desc}
         line = {
             "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "N_st": Nst, "slabs_per_step": 1,
+            "config": {"workload": W["name"] if args.n == W["n"] else W["name"] + " (profiling run: n=%d)" % args.n,
+                       "N_st": Nst, "slabs_per_step": 1,
                        "smoother": {"nu1": args.smooth, "nu2": args.smooth, "omega": "1.2/2^d", "omega_p": 1.0,
                                     "inverse_storage": "fp16" if args.vanka_fp16 else "fp32"},
-                       "l2": "working set larger than L2 (Vanka patch inverses 3.4 GB)",
+                       "l2": "working set larger than L2 (finest-level patch inverses %.2f GB)" % _inverse_gb(w, args),
                        "parallelism": "replicas" if ws > 1 else "single"},
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
             "clocks": clk.summary(),
@@ -346,6 +368,14 @@ def _peaks():
 VANKA_DRAM_BYTES_PER_CELL = 188.586752e6 / 9216
 
 
+def _inverse_gb(w, args):
+    """Bytes of the finest level's time-diagonalised patch inverses."""
+    from math import comb
+    ms = w["d"] * (w["r"] + 2) ** w["d"] + comb(w["r"] + w["d"], w["d"])
+    st = (ms + 7) // 8 * 8
+    return args.n ** w["d"] * (w["k"] + 1) * ms * st * (2 if args.vanka_fp16 else 4) / 1e9
+
+
 def roofline(S, prof, args):
     """Finest-level Vanka patch apply (the dominant kernel): per colour launch it reads the
     time-diagonalised patch inverses of its cells ((k+1) m_s^2 reals each), gathers the residual
@@ -357,10 +387,9 @@ def roofline(S, prof, args):
     if not k or not k["count"]:
         return None
     achieved = k["bytes"] / (k["ms"] * 1e-3) / 1e9
-    cells = (args.n // 2) ** 2                     # cells of one colour launch on the finest level
-    traffic = (VANKA_DRAM_BYTES_PER_CELL * cells
-               if (args.vanka_fp16 == 0 and WORKLOAD["d"] == 2 and WORKLOAD["r"] == 2 and WORKLOAD["k"] == 2)
-               else None)
+    d = WORKLOADS[args.workload]["d"]
+    cells = (args.n // 2) ** d                     # cells of one colour launch on the finest level
+    traffic = VANKA_DRAM_BYTES_PER_CELL * cells if (args.vanka_fp16 == 0 and args.workload == "2d") else None
     return {"bound": "hbm", "kernel": "k_vanka_apply (finest level)", "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
             "algorithmic_bytes_per_launch": k["bytes"] / k["count"],
