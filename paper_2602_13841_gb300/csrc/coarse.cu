@@ -73,12 +73,95 @@ __global__ void k_transpose32(float* S, int n) {
   }
 }
 
+// Gauss-Jordan step p of a large coarse matrix (row-major, in place), the same arithmetic as
+// gauss_jordan spread over launches: k_gj_pivot (one block) picks and swaps the pivot row,
+// scales it and moves column p into `col`; k_gj_elim (all SMs) updates the other rows; after the
+// last step k_gj_unswap (one block) undoes the column exchanges.  A zero pivot sets *status and
+// turns the remaining steps into no-ops.
+__global__ void k_gj_pivot(float* S, int n, int p, float* col, int* piv, int* status) {
+  __shared__ int s_r;
+  __shared__ float s_best[32];
+  __shared__ int s_idx[32];
+  if (*status) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  float best = -1.f; int bi = p;
+  for (int i = p + tid; i < n; i += nt) {
+    const float a = fabsf(S[(int64_t)i * n + p]);
+    if (a > best || (a == best && i < bi)) { best = a; bi = i; }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ob = __shfl_down_sync(0xffffffffu, best, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if ((tid & 31) == 0) { s_best[tid >> 5] = best; s_idx[tid >> 5] = bi; }
+  __syncthreads();
+  if (tid < 32) {
+    best = tid < (nt >> 5) ? s_best[tid] : -1.f;
+    bi = tid < (nt >> 5) ? s_idx[tid] : p;
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ob = __shfl_down_sync(0xffffffffu, best, off);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (tid == 0) { s_r = bi; piv[p] = bi; if (!(best > 0.f)) *status = 1; }
+  }
+  __syncthreads();
+  if (*status) return;
+  const int r = s_r;
+  if (r != p)
+    for (int j = tid; j < n; j += nt) {
+      const float t = S[(int64_t)p * n + j]; S[(int64_t)p * n + j] = S[(int64_t)r * n + j]; S[(int64_t)r * n + j] = t;
+    }
+  __syncthreads();
+  const float pinv = 1.f / S[(int64_t)p * n + p];
+  __syncthreads();
+  for (int j = tid; j < n; j += nt) S[(int64_t)p * n + j] = (j == p) ? pinv : S[(int64_t)p * n + j] * pinv;
+  for (int i = tid; i < n; i += nt) {
+    col[i] = (i == p) ? 0.f : S[(int64_t)i * n + p];
+    if (i != p) S[(int64_t)i * n + p] = 0.f;
+  }
+}
+
+__global__ void k_gj_elim(float* S, int n, int p, const float* __restrict__ col, const int* status) {
+  if (*status) return;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    if (i != p) S[e] -= col[i] * S[(int64_t)p * n + j];
+  }
+}
+
+__global__ void k_gj_unswap(float* S, int n, const int* __restrict__ piv, const int* status) {
+  if (*status) return;
+  for (int p = n - 1; p >= 0; --p) {
+    const int r = piv[p];
+    if (r != p)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float t = S[(int64_t)i * n + p]; S[(int64_t)i * n + p] = S[(int64_t)i * n + r]; S[(int64_t)i * n + r] = t;
+      }
+    __syncthreads();
+  }
+}
+
 cudaError_t coarse_invert(const double* A, float* Ainv, float* col, int* piv, int Nb, int* status,
                           cudaStream_t s) {
   k_to_rowmajor32<<<152 * 4, 256, 0, s>>>(A, Ainv, Nb);
   note_launch();
-  k_gj_single<<<1, 1024, 0, s>>>(Ainv, Nb, col, piv, status);
+  if (Nb <= 512) {
+    k_gj_single<<<1, 1024, 0, s>>>(Ainv, Nb, col, piv, status);
+    note_launch();
+  } else {
+    // large coarse systems (3D): one pivot launch and one all-SM elimination launch per step
+    for (int p = 0; p < Nb; ++p) {
+      k_gj_pivot<<<1, 1024, 0, s>>>(Ainv, Nb, p, col, piv, status);
+      k_gj_elim<<<152 * 4, 256, 0, s>>>(Ainv, Nb, p, col, status);
+    }
+    k_gj_unswap<<<1, 1024, 0, s>>>(Ainv, Nb, piv, status);
+    note_launch(2 * Nb + 1);
+  }
   k_transpose32<<<152 * 4, 256, 0, s>>>(Ainv, Nb);    // row-major inverse -> column-major
+  note_launch();
   return cudaGetLastError();
 }
 

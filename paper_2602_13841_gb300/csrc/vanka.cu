@@ -130,7 +130,8 @@ static cudaError_t build_dn(const Level& lv, const Problem& pb, const T* U, T* v
     V.ebase = e0;
     k_elem<T, D, N><<<(unsigned)(e1 - e0), 256, es, s>>>(V, tb, e0, e1);
     if (onchip) {
-      k_patch<T, D, N><<<(unsigned)(p1 - p0), 256, ps, s>>>(V, tb, te, p0, p1);
+      // 3D patches (m_s = 85 for Q2/P1): more threads shorten each elimination step
+      k_patch<T, D, N><<<(unsigned)(p1 - p0), D == 3 ? 512 : 256, ps, s>>>(V, tb, te, p0, p1);
     } else {
       const int64_t grid = p1 - p0 < kWorkSlots ? p1 - p0 : kWorkSlots;
       k_patch_global<T, D, N><<<(unsigned)grid, 512, ps, s>>>(V, tb, te, p0, p1);
