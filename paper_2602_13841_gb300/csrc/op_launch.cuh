@@ -80,7 +80,8 @@ static cudaError_t launch_dn(const Level& lv, const Problem& pb, double t0, cons
       note_launch();
     }
     if (D == 3 && MODE != MM && lv.nbcells[c] > 0) {       // 2D: faces fused into k_volume2d
-      dim3 grid((lv.nbcells[c] + fcpb - 1) / fcpb, batch);
+      // one block per (boundary cell, time node) when fcpb == 1
+      dim3 grid(fcpb == 1 ? lv.nbcells[c] * kp1 : (lv.nbcells[c] + fcpb - 1) / fcpb, batch);
       k_faces<T, D, N, MODE><<<grid, fcpb * Q, fsmem, stream>>>(A, tb, lv.bcells[c], lv.nbcells[c], fcpb);
       note_launch();
     }

@@ -344,7 +344,10 @@ __global__ void k_faces(OpArgs<T> A, Tab<T> tb_p, const int* __restrict__ bcells
   T(*corner)[3] = reinterpret_cast<T(*)[3]>(s_sc + 4);
 
   constexpr bool RES = (MODE == MR);
-  const int bi = blockIdx.x * cpb + g;
+  // with cpb == 1 each block serves one time node a0 of one cell (the time nodes' face terms are
+  // independent and write different parts of y); with cpb > 1 a block loops over all time nodes
+  const int a_lo = cpb == 1 ? (int)(blockIdx.x % kp1) : 0, a_hi = cpb == 1 ? a_lo + 1 : kp1;
+  const int bi = cpb == 1 ? (int)(blockIdx.x / kp1) : blockIdx.x * cpb + g;
   const bool on = (g < cpb) && (bi < nb);
   const LevelArgs<T>& L = A.L;
   A.x += blockIdx.y * A.xs;
@@ -360,14 +363,14 @@ __global__ void k_faces(OpArgs<T> A, Tab<T> tb_p, const int* __restrict__ bcells
   const int64_t poff = (int64_t)kp1 * L.Nv;
   if (on) {
     load_corners<T, D>(L, cc, corner, t);
-    for (int b = 0; b < kp1; ++b)
+    for (int b = a_lo; b < a_hi; ++b)
       for (int c = 0; c < D; ++c) {
         int64_t gi = (int64_t)b * L.Nv + c * L.nnodes + gnode;
         s_u[(b * D + c) * Q + t] = A.x[gi];
         s_st[(b * D + c) * Q + t] = RES ? A.x[gi] : A.state[gi];
       }
     if (t < npc)
-      for (int b = 0; b < kp1; ++b) s_pm[b * MAXNP + t] = A.x[poff + (int64_t)b * L.Np + cell * npc + t];
+      for (int b = a_lo; b < a_hi; ++b) s_pm[b * MAXNP + t] = A.x[poff + (int64_t)b * L.Np + cell * npc + t];
   }
   __syncthreads();
   // cell volume |K|
@@ -411,7 +414,7 @@ __global__ void k_faces(OpArgs<T> A, Tab<T> tb_p, const int* __restrict__ bcells
       if (has && t == 0) { T v = 0; for (int p = 0; p < NF; ++p) v += s_red[p]; s_sc[1] = v; }
       __syncthreads();
       const T h = has ? s_sc[0] / s_sc[1] * L.hscale : (T)1;
-      for (int a = 0; a < kp1; ++a) {
+      for (int a = a_lo; a < a_hi; ++a) {
         if (has && t < NF) {
           T dv[3] = {0, 0, 0}, v[3] = {0, 0, 0}, gref[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
           constexpr int NN = Shape<D, N>::Q;
