@@ -185,7 +185,10 @@ __device__ inline T invert(const T (*J)[3], T (*G)[3]) {
 // TG2D: Taylor-Green vortex (exact solution, f = 0, g = v); MMS2D: manufactured solution of
 // the convergence test (second component with a minus sign so that div v = 0), g = 0;
 // TG3D: Taylor-Green initial field, g = v0, f = 0; MMS3D: sin t sin(pi z)(pi sin^2(pi x)
-// sin(2 pi y), -pi sin(2 pi x) sin^2(pi y), 0) with p = sin t prod sin cos, g = 0.
+// sin(2 pi y), -pi sin(2 pi x) sin^2(pi y), 0) with p = sin t prod sin cos, g = 0; CAV3D: the
+// lid-driven cavity of Sec. 5.2, g = (sin(pi t / 4), 0, 0) on the lid z = 1, zero on the other
+// walls, f = 0, v0 = 0.  Face quadrature points are interior to their faces, so z = 1 (up to
+// rounding of the multilinear map) holds exactly on the lid's points and nowhere else.
 __device__ inline void problem_velocity_tg2d(const double* x, double t, double nu, double* v) {
   const double pi = 3.141592653589793238;
   double F = exp(-2.0 * pi * pi * nu * t);
@@ -202,6 +205,8 @@ __device__ inline void problem_g(int problem, const double* x, double t, double 
   } else if (problem == 2 && D == 3) {
     g[0] = sin(pi * x[0]) * cos(pi * x[1]) * cos(pi * x[2]);
     g[1] = -cos(pi * x[0]) * sin(pi * x[1]) * cos(pi * x[2]);
+  } else if (problem == 4 && D == 3) {
+    if (x[2] > 1.0 - 1e-9) g[0] = sin(0.25 * pi * t);
   }
 }
 

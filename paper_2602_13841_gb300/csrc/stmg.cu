@@ -198,7 +198,7 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
 }
 
 stmg_status stmg_set_physics(stmg_handle* hh, double nu, double tau, int problem) {
-  if (!hh || !(nu > 0) || !(tau > 0) || problem < 0 || problem > 3) return STMG_ERR_ARG;
+  if (!hh || !(nu > 0) || !(tau > 0) || problem < STMG_TG2D || problem > STMG_CAV3D) return STMG_ERR_ARG;
   Handle* h = reinterpret_cast<Handle*>(hh);
   h->prm.nu = nu; h->prm.tau = tau; h->prm.problem = problem;
   h->pb.nu = nu; h->pb.tau = tau; h->pb.problem = problem;
@@ -213,7 +213,8 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
   if (!p || !out) return STMG_ERR_ARG;
   *out = nullptr;
   if (p->dim < 2 || p->dim > 3 || p->r < 1 || p->r > 3 || p->k < 0 || p->k > 2 ||
-      p->n_cells_1d < 1 || p->n_cells_1d > 4096 || !(p->tau > 0) || !(p->nu > 0))
+      p->n_cells_1d < 1 || p->n_cells_1d > 4096 || !(p->tau > 0) || !(p->nu > 0) ||
+      p->problem < STMG_TG2D || p->problem > STMG_CAV3D)
     return STMG_ERR_ARG;
   auto h = std::make_unique<Handle>();
   h->prm = *p;

@@ -11,7 +11,7 @@ LIBPATH = os.path.join(_HERE, "libstmg.so")
 _lib = None
 
 STMG_FP64, STMG_FP32 = 0, 1
-PROBLEMS = {"TG2D": 0, "MMS2D": 1, "TG3D": 2, "MMS3D": 3}
+PROBLEMS = {"TG2D": 0, "MMS2D": 1, "TG3D": 2, "MMS3D": 3, "CAV3D": 4}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NOT_CONVERGED",
           5: "ERR_NUMERIC", 6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
 

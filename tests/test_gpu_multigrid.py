@@ -119,6 +119,7 @@ def test_smoother_and_vcycle_match_oracle(d, n, r, k, amp, prec):
     ("fp32", 3, 4, 1, 0, 0.0, 1e-2, 0.05, "MMS3D"),
     ("fp32", 3, 4, 1, 2, 0.1, 1.0 / 400, 0.01, "MMS3D"),   # small case of the 3D Q2/P1/DG(2) workload
     ("fp32", 3, 4, 2, 1, 0.0, 1.0 / 1600, 0.02, "TG3D"),   # small case of the 3D Q3/P2/DG(1) workload
+    ("fp32", 3, 4, 2, 2, 0.0, 4e-4, 1.0 / 32, "CAV3D"),    # small case of the lid-driven cavity (Sec. 5.2)
 ])
 def test_slab_solve_reaches_tolerance_and_matches_exact_solution(precision, d, n, r, k, amp, nu, tau, pname):
     import torch

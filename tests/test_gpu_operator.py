@@ -67,7 +67,8 @@ def test_apply_fp64_and_fp32_match_oracle(d, n, r, k, amp):
 
 
 @pytest.mark.parametrize("d,n,r,k,amp,pname", [(2, 5, 1, 1, 0.0, "TG2D"), (2, 6, 2, 2, 0.15, "MMS2D"),
-                                               (3, 3, 1, 2, 0.15, "MMS3D"), (3, 3, 2, 1, 0.1, "TG3D")])
+                                               (3, 3, 1, 2, 0.15, "MMS3D"), (3, 3, 2, 1, 0.1, "TG3D"),
+                                               (3, 3, 2, 2, 0.1, "CAV3D")])
 def test_residual_matches_oracle(d, n, r, k, amp, pname):
     import torch
     S, verts = _solver(d, n, r, k, amp, seed=3, problem=pname)
@@ -86,7 +87,7 @@ def test_residual_matches_oracle(d, n, r, k, amp, pname):
     assert err < 1e-12, err
 
 
-@pytest.mark.parametrize("d,pname", [(2, "TG2D"), (3, "TG3D")])
+@pytest.mark.parametrize("d,pname", [(2, "TG2D"), (3, "TG3D"), (3, "CAV3D")])
 def test_initial_condition_is_nodal_interpolant(d, pname):
     import torch
     n, r = 4, 2
