@@ -185,6 +185,8 @@ def main():
     ap.add_argument("--vanka-fp16", type=int, default=-1, help="1: FP16 storage of the patch inverses "
                                                                    "(-1: the workload's choice)")
     ap.add_argument("--smooth", type=int, default=0, help="Vanka pre- and post-sweeps per level (0: the workload's)")
+    ap.add_argument("--keep-time-degree", type=int, default=0,
+                    help="1: p-coarsen in space only, DG(k) on every level (a variant of the paper's order)")
     ap.add_argument("--serving-requests", type=int, default=16,
                     help="requests of the serving leg (Poisson stream, 20/s); 0 skips it")
     args = ap.parse_args()
@@ -215,6 +217,7 @@ def main():
                             problem=w["problem"], precond_precision=stmg.STMG_FP32, newton_rtol=w["rtol"],
                             newton_atol=w["atol"], vanka_fp16=int(args.vanka_fp16),
                             gmres_restart=w["restart"], gmres_maxit=w["restart"],
+                            keep_time_degree=int(args.keep_time_degree),
                             **dict(SMOOTH, nu1=args.smooth, nu2=args.smooth))
     stream = torch.cuda.Stream(device=dev)
     S = stmg.Solver(p, inputs.vertices(w["d"], w["n"], w["amp"], w["seed"]), stream=stream.cuda_stream)
@@ -334,6 +337,8 @@ def main():
                        "N_st": Nst, "slabs_per_step": 1,
                        "smoother": {"nu1": args.smooth, "nu2": args.smooth, "omega": "1.2/2^d", "omega_p": 1.0,
                                     "inverse_storage": "fp16" if args.vanka_fp16 else "fp32"},
+                       "coarsening": ("p in space only, DG(k) on every level, then h" if args.keep_time_degree
+                                      else "p in space and time ((k,r) -> (k/2,r/2)), then h"),
                        "l2": "working set larger than L2 (finest-level patch inverses %.2f GB)" % _inverse_gb(w, args),
                        "parallelism": "replicas" if ws > 1 else "single"},
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,

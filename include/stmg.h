@@ -84,6 +84,10 @@ typedef struct {
   int build_chunk_cells; /* the smoother build computes the per-cell element matrices in chunks of
                           whole cell planes of at most this many cells (at least three planes),
                           bounding its scratch memory; <= 0 (default): 262144 */
+  int keep_time_degree; /* 0 (default): the paper's coarsening order, p in space and time
+                          ((k, r) -> (k/2, r/2), Sec. 4.2).  1: p-coarsen in space only and keep
+                          DG(k) on every level (a variant; the coarse levels cost (k+1)/(k/2+1)
+                          times more, the V-cycle contracts faster when k >= 2) */
 } stmg_params;
 
 /* Fill *p with the paper's defaults (Sec. 5, Alg. 1-2) for a d-dimensional problem. */

@@ -43,11 +43,12 @@ def height(x):
     return h
 
 
-def hierarchy(d, n, r, k, vertices, max_h=-1):
-    """List of (n, r, k, vertices) from fine to coarse."""
+def hierarchy(d, n, r, k, vertices, max_h=-1, keep_k=False):
+    """List of (n, r, k, vertices) from fine to coarse.  keep_k: p-coarsen in space only and keep
+    DG(k) on every level (a variant of the paper's order, which halves k as well)."""
     levels = [(n, r, k, np.asarray(vertices, float))]
-    while height(r) > 0 or height(k) > 0:
-        if height(r) > height(k):
+    while height(r) > 0 or (height(k) > 0 and not keep_k):
+        if keep_k or height(r) > height(k):
             r //= 2
         elif height(k) > height(r):
             k //= 2
@@ -242,14 +243,14 @@ class Multigrid:
     """hp-STMG V-cycle: z = B^{-1} r on the finest level (Sec. 4.2)."""
 
     def __init__(self, d, n, r, k, vertices, tau, nu, omega=None, nu1=1, nu2=1, omega_p=1.0,
-                 gamma=(10.0, 10.0), bconv=True, max_h=-1):
+                 gamma=(10.0, 10.0), bconv=True, max_h=-1, keep_k=False):
         # Eq. vanka0 leaves omega open; the additive sum puts each velocity vertex in up to 2^d
         # patches, so the default damping is 1.2 / 2^d (0.3 in 2D, 0.15 in 3D)
         if omega is None:
             omega = 1.2 / 2 ** d
         p0 = r + 1
         self.levels = [Level(d, ln, lr, lk, lv, tau, nu, gamma, bconv, hscale=(ln / n) / (p0 * (p0 + 1)))
-                       for ln, lr, lk, lv in hierarchy(d, n, r, k, vertices, max_h)]
+                       for ln, lr, lk, lv in hierarchy(d, n, r, k, vertices, max_h, keep_k)]
         self.P, self.I = [], []
         for f, c in zip(self.levels[:-1], self.levels[1:]):
             P, I = transfer(f, c)

@@ -32,6 +32,20 @@ long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 int height(int x) { int h = 0; while (x > 1) { x /= 2; ++h; } return h; }
 
+// (r, k) of the p-levels, finest first (Sec. 4.2): the taller of the space and time degree
+// hierarchies is halved alone until the heights match, then both, down to (1, 1); with
+// keep_time the time degree stays k and only r is halved.
+std::vector<std::pair<int, int>> p_hierarchy(int r, int k, int keep_time) {
+  std::vector<std::pair<int, int>> pk{{r, k}};
+  while (height(r) > 0 || (!keep_time && height(k) > 0)) {
+    if (keep_time || height(r) > height(k)) r /= 2;
+    else if (height(k) > height(r)) k /= 2;
+    else { r /= 2; k /= 2; }
+    pk.push_back({r, k});
+  }
+  return pk;
+}
+
 stmg_status Handle::fail(stmg_status s, const std::string& msg) {
   err = msg;
   return s;
@@ -151,14 +165,8 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
     return STMG_ERR_ARG;
   const int d = p->dim, n = p->n_cells_1d;
   std::vector<std::array<int, 3>> lv;     // (n, r, k) of every level, same rule as stmg_create
-  int r = p->r, k = p->k;
-  lv.push_back({n, r, k});
-  while (height(r) > 0 || height(k) > 0) {
-    if (height(r) > height(k)) r /= 2;
-    else if (height(k) > height(r)) k /= 2;
-    else { r /= 2; k /= 2; }
-    lv.push_back({n, r, k});
-  }
+  for (auto& rk : p_hierarchy(p->r, p->k, p->keep_time_degree)) lv.push_back({n, rk.first, rk.second});
+  const int r = lv.back()[1], k = lv.back()[2];
   int nn = n, hl = 0;
   while (nn % 2 == 0 && nn / 2 >= 2 && (p->n_levels_h < 0 || hl < p->n_levels_h)) { nn /= 2; ++hl; lv.push_back({nn, r, k}); }
   const double es = p->precond_precision == STMG_FP32 ? 4.0 : 8.0;
@@ -239,14 +247,8 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
   // hierarchy: p-coarsening first (taller of the r / k hierarchies alone until the heights
   // match, then both), then h-coarsening of the space mesh (Sec. 4.2, "cycle and coarsening order")
   try {
-    int r = p->r, k = p->k;
-    std::vector<std::pair<int, int>> pk{{r, k}};
-    while (height(r) > 0 || height(k) > 0) {
-      if (height(r) > height(k)) r /= 2;
-      else if (height(k) > height(r)) k /= 2;
-      else { r /= 2; k /= 2; }
-      pk.push_back({r, k});
-    }
+    std::vector<std::pair<int, int>> pk = p_hierarchy(p->r, p->k, p->keep_time_degree);
+    const int r = pk.back().first, k = pk.back().second;
     const double p0 = p->r + 1;
     for (auto& rk : pk) {
       Level lv; lv.d = d; lv.n = n; lv.r = rk.first; lv.k = rk.second;

@@ -37,7 +37,7 @@ def _setup(d, n, r, k, amp, precision="fp64", omega=None, nu=0.01, tau=0.05, pro
     p = stmg.default_params(dim=d, n_cells_1d=n, r=r, k=k, nu=nu, tau=tau, problem=problem,
                             omega=omega or 0.0, precond_precision=prec, **kw)
     S = stmg.Solver(p, verts)
-    mg = multigrid.Multigrid(d, n, r, k, verts, tau, nu, omega=omega)
+    mg = multigrid.Multigrid(d, n, r, k, verts, tau, nu, omega=omega, keep_k=bool(kw.get("keep_time_degree", 0)))
     return S, mg, verts
 
 
@@ -69,16 +69,19 @@ def test_transfers_match_oracle(d, n, r, k, amp, prec):
         assert _rel(_np(outc)[:nvc], mg.I[l] @ xf[:(f.k + 1) * f.lay.Nv]) < tol
 
 
-@pytest.mark.parametrize("d,n,r,k,amp,prec", [(2, 8, 2, 2, 0.15, "fp64"), (2, 8, 1, 1, 0.0, "fp64"),
-                                              (2, 6, 1, 0, 0.1, "fp64"), (2, 8, 2, 2, 0.15, "fp32"),
-                                              (3, 4, 1, 1, 0.1, "fp32"),
-                                              # 3D Q3/P2: patches beyond shared memory (global path)
-                                              (3, 2, 2, 1, 0.1, "fp64"), (3, 4, 2, 1, 0.0, "fp32")])
-def test_smoother_and_vcycle_match_oracle(d, n, r, k, amp, prec):
+@pytest.mark.parametrize("d,n,r,k,amp,prec,keep", [(2, 8, 2, 2, 0.15, "fp64", 0), (2, 8, 1, 1, 0.0, "fp64", 0),
+                                                   (2, 6, 1, 0, 0.1, "fp64", 0), (2, 8, 2, 2, 0.15, "fp32", 0),
+                                                   (3, 4, 1, 1, 0.1, "fp32", 0),
+                                                   # 3D Q3/P2: patches beyond shared memory (global path)
+                                                   (3, 2, 2, 1, 0.1, "fp64", 0), (3, 4, 2, 1, 0.0, "fp32", 0),
+                                                   # p-coarsening in space only, DG(k) on every level
+                                                   (2, 8, 2, 2, 0.15, "fp64", 1), (3, 4, 1, 2, 0.1, "fp32", 1)])
+def test_smoother_and_vcycle_match_oracle(d, n, r, k, amp, prec, keep):
     """FP64: tight tolerances.  FP32 (the mixed-precision preconditioner): the error of each
     result against the FP64 oracle is bounded by 2e-3 relative (ill-conditioned patches)."""
     import torch
-    S, mg, _ = _setup(d, n, r, k, amp, precision=prec)
+    S, mg, _ = _setup(d, n, r, k, amp, precision=prec, keep_time_degree=keep)
+    assert [(L["n"], L["r"], L["k"]) for L in S.levels] == [(L.n, L.r, L.k) for L in mg.levels]
     dt = S.pdtype
     tol_s, tol_v, tol_x = (1e-9, 1e-8, 1e-13) if prec == "fp64" else (2e-3, 2e-3, 2e-6)
     L0 = mg.levels[0]
@@ -120,11 +123,13 @@ def test_smoother_and_vcycle_match_oracle(d, n, r, k, amp, prec):
     ("fp32", 3, 4, 1, 2, 0.1, 1.0 / 400, 0.01, "MMS3D"),   # small case of the 3D Q2/P1/DG(2) workload
     ("fp32", 3, 4, 2, 1, 0.0, 1.0 / 1600, 0.02, "TG3D"),   # small case of the 3D Q3/P2/DG(1) workload
     ("fp32", 3, 4, 2, 2, 0.0, 4e-4, 1.0 / 32, "CAV3D"),    # small case of the lid-driven cavity (Sec. 5.2)
+    ("fp32+keep", 2, 8, 2, 2, 0.1, 1e-3, 0.05, "TG2D"),    # p-coarsening in space only
 ])
 def test_slab_solve_reaches_tolerance_and_matches_exact_solution(precision, d, n, r, k, amp, nu, tau, pname):
     import torch
-    S, mg, verts = _setup(d, n, r, k, amp, precision=precision, nu=nu, tau=tau, problem=pname,
-                          newton_rtol=1e-10, newton_atol=0.0)
+    keep = int(precision.endswith("+keep"))
+    S, mg, verts = _setup(d, n, r, k, amp, precision=precision.split("+")[0], nu=nu, tau=tau, problem=pname,
+                          newton_rtol=1e-10, newton_atol=0.0, keep_time_degree=keep)
     L0 = mg.levels[0]
     prob = problems.make(pname, nu)
     V0 = torch.empty(L0.lay.Nv, dtype=torch.float64, device="cuda")

@@ -156,3 +156,37 @@ def test_vcycle_iteration_contracts(d, n, r, k, nu, rate):
         x = x + mg.vcycle(b - J @ x)
     red = (np.linalg.norm(b - J @ x) / r0) ** (1.0 / 6.0)
     assert red < rate, red
+
+
+def test_hierarchy_follows_the_coarsening_order():
+    """Sec. 4.2: p first, (k, r) -> (k/2, r/2) with the taller hierarchy alone until the heights
+    match, then h down to two cells per direction; keep_k (a variant) halves r only."""
+    V = inputs.vertices(2, 8, 0.0, 1)
+    rk = lambda lv: [(n, r, k) for n, r, k, _ in lv]
+    assert rk(multigrid.hierarchy(2, 8, 2, 2, V)) == [(8, 2, 2), (8, 1, 1), (4, 1, 1), (2, 1, 1)]
+    assert rk(multigrid.hierarchy(2, 8, 3, 1, V)) == [(8, 3, 1), (8, 1, 1), (4, 1, 1), (2, 1, 1)]
+    assert rk(multigrid.hierarchy(2, 8, 1, 2, V)) == [(8, 1, 2), (8, 1, 1), (4, 1, 1), (2, 1, 1)]
+    assert rk(multigrid.hierarchy(2, 8, 2, 2, V, keep_k=True)) == [(8, 2, 2), (8, 1, 2), (4, 1, 2), (2, 1, 2)]
+    assert rk(multigrid.hierarchy(2, 8, 1, 2, V, keep_k=True)) == [(8, 1, 2), (4, 1, 2), (2, 1, 2)]
+
+
+def test_vcycle_with_space_only_p_coarsening_contracts():
+    """The variant hierarchy (DG(2) on every level) as a stationary iteration: the Galerkin
+    identity holds on it too, and it contracts at least as fast as the paper's order here."""
+    from oracle import problems
+    d, n, r, k, nu = 2, 8, 2, 2, 1e-3
+    verts = inputs.vertices(d, n, 0.1, 9)
+    prob = problems.make("TG2D", nu)
+    red = {}
+    for keep in (False, True):
+        mg = multigrid.Multigrid(d, n, r, k, verts, 0.05, nu, keep_k=keep)
+        L = mg.levels[0]
+        V = forms.interpolate_velocity(L.space, prob.v0)
+        mg.setup(np.concatenate([np.tile(V, k + 1), np.zeros((k + 1) * L.lay.Np)]))
+        J = mg.J[0]
+        b = J @ inputs.uniform(L.Nst, 6)
+        x = np.zeros(L.Nst)
+        for _ in range(6):
+            x = x + mg.vcycle(b - J @ x)
+        red[keep] = (np.linalg.norm(b - J @ x) / np.linalg.norm(b)) ** (1.0 / 6.0)
+    assert red[True] < 0.6 and red[True] <= red[False] * 1.05, red
