@@ -149,34 +149,33 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
   const Level& lv = h->levels[l];
   const double omega = h->prm.omega;
   for (int it = 0; it < nsweeps; ++it) {
-    const T* jd = nullptr;
+    const T* res = rhs;
     if (it == 0 && zero_start) {
       CKE(cudaMemsetAsync(d, 0, lv.Nst * sizeof(T), s));
     } else {
-      // q = J d; the Vanka apply gathers rhs - q on its patches
+      // q = rhs - J d
       h->kbegin(KC_APPLYP);
       CKE(launch_operator<T>(lv, h->pb, OP_JAC, 0.0, d, U[l], nullptr, q[l], s));
       h->kend(KC_APPLYP);
-      jd = q[l];
+      CKE(vaxpby<T>(lv.Nst, (T)1, rhs, (T)-1, q[l], s));
+      res = q[l];
     }
     // one timer span over the colour launches of the sweep (they run back to back);
     // algorithmic bytes: the patch inverses of every cell, residual gather, d read and write
     // per cell: (k+1) m_s^2 stored reals (one spatial inverse per real time eigenvalue, a complex
-    // one per conjugate pair), gather of rhs (and of J d after the first sweep) and d update on
-    // the (k+1) m_s patch DoFs
+    // one per conjugate pair), residual gather and d update on the (k+1) m_s patch DoFs
     const double ms = (double)vanka_spatial_size(lv), m = (double)vanka_patch_size(lv);
     const double ib = (lv.k + 1) * ms * ms * (invh[l] ? 2.0 : (double)sizeof(T)) + (invh[l] ? 4.0 * (lv.k + 1) : 0.0);
     int64_t cells = 0;
     h->kbegin(KC_VANKA_APPLY);
     if (l == 0) h->kbegin(KC_VANKA_APPLY0);
     for (int c = 0; c < lv.ncolors; ++c) {
-      CKE(vanka_apply<T>(lv, h->pb, inv[l], invh[l], iscale[l], rhs, d, omega, h->prm.omega_p, c, wstat, s,
-                         h->wait_fault ? 16u : 0u, jd));
+      CKE(vanka_apply<T>(lv, h->pb, inv[l], invh[l], iscale[l], res, d, omega, h->prm.omega_p, c, wstat, s,
+                         h->wait_fault ? 16u : 0u));
       cells += lv.colors[c].count;
     }
-    const double vb = (jd ? 4.0 : 3.0) * m * sizeof(T);
-    if (l == 0) h->kend(KC_VANKA_APPLY0, (double)cells * (ib + vb), lv.ncolors);
-    h->kend(KC_VANKA_APPLY, (double)cells * (ib + vb), lv.ncolors);
+    if (l == 0) h->kend(KC_VANKA_APPLY0, (double)cells * (ib + 3.0 * m * sizeof(T)), lv.ncolors);
+    h->kend(KC_VANKA_APPLY, (double)cells * (ib + 3.0 * m * sizeof(T)), lv.ncolors);
   }
   return cudaSuccess;
 }

@@ -75,8 +75,7 @@ size_t vanka_elem_cells(const Level& lv);   // cells per chunk of the element-ma
 template <typename T>
 cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
                         const T* res, T* d, double omega, double omega_p, int color, int* wstat, cudaStream_t s,
-                        unsigned extra_tx = 0,    // extra_tx: failure-test hook (see stmg_test_wait_timeout)
-                        const T* jd = nullptr);   // non-null: the residual is res - jd (jd = J d of the sweep)
+                        unsigned extra_tx = 0);   // extra_tx: failure-test hook (see stmg_test_wait_timeout)
 size_t vanka_spatial_size(const Level& lv);          // m_s = d (r+2)^d + npc
 size_t vanka_patch_size(const Level& lv);            // m_st = (k+1) m_s
 size_t vanka_inv_entries(const Level& lv);           // stored reals of one cell's patch inverse ((k+1) m_s x stride)

@@ -156,7 +156,7 @@ cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar
 
 template <typename T, typename SI, int D, int N>
 static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv, const float* scale, const T* res,
-                               const T* jd, T* d, double omega, double omega_p, const ColorInfo& ci, int* wstat,
+                               T* d, double omega, double omega_p, const ColorInfo& ci, int* wstat,
                                unsigned extra_tx, cudaStream_t s) {
   // one block per cell, threads = spatial patch rows rounded up to whole warps
   const int ms = (int)vanka_spatial_size(lv), kp1 = lv.k + 1;
@@ -165,7 +165,7 @@ static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv
     const int mr = (ms + 1) & ~1;
     const size_t gsm = (((size_t)kp1 * mr * sizeof(T) + 7) & ~(size_t)7) + (size_t)ms * 8;
     k_vanka_apply_global<T, SI, D, N><<<(unsigned)ci.count, threads, gsm, s>>>(
-        level_args<T>(lv, pb, 0.0), inv, scale, res, jd, d, (T)omega, (T)omega_p, kp1, lv.npc,
+        level_args<T>(lv, pb, 0.0), inv, scale, res, d, (T)omega, (T)omega_p, kp1, lv.npc,
         make_teig<T>(lv.tabs, pb.tau), ci);
     return cudaSuccess;
   }
@@ -177,7 +177,7 @@ static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv
   cudaError_t e = allow_smem(k_vanka_apply<T, SI, D, N>, smem);
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((ci.count + cpb - 1) / cpb);
-  k_vanka_apply<T, SI, D, N><<<blocks, threads * cpb, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, scale, res, jd, d,
+  k_vanka_apply<T, SI, D, N><<<blocks, threads * cpb, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, scale, res, d,
                                                                        (T)omega, (T)omega_p, kp1, lv.npc,
                                                                        make_teig<T>(lv.tabs, pb.tau), ci, wstat, extra_tx);
   return cudaSuccess;
@@ -185,14 +185,14 @@ static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv
 
 template <typename T, int D, int N>
 static cudaError_t apply_dn(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
-                            const T* res, const T* jd, T* d, double omega, double omega_p, int color, int* wstat,
+                            const T* res, T* d, double omega, double omega_p, int color, int* wstat,
                             unsigned extra_tx, cudaStream_t s) {
   const ColorInfo& ci = lv.colors[color];
   if (ci.count == 0) return cudaSuccess;
-  cudaError_t e = invh ? apply_cells<T, __half, D, N>(lv, pb, (const __half*)invh, scale, res, jd, d, omega, omega_p,
-                                                      ci, wstat, extra_tx, s)
-                       : apply_cells<T, T, D, N>(lv, pb, inv, nullptr, res, jd, d, omega, omega_p, ci, wstat,
-                                                 extra_tx, s);
+  cudaError_t e = invh ? apply_cells<T, __half, D, N>(lv, pb, (const __half*)invh, scale, res, d, omega, omega_p, ci,
+                                                      wstat, extra_tx, s)
+                       : apply_cells<T, T, D, N>(lv, pb, inv, nullptr, res, d, omega, omega_p, ci, wstat, extra_tx,
+                                                 s);
   if (e != cudaSuccess) return e;
   note_launch();
   return cudaGetLastError();
@@ -206,9 +206,9 @@ size_t vanka_inv_entries(const Level& lv) {
 template <typename T>
 cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
                         const T* res, T* d, double omega, double omega_p, int color, int* wstat, cudaStream_t s,
-                        unsigned extra_tx, const T* jd) {
+                        unsigned extra_tx) {
   const int N = lv.r + 2;
-#define STMG_A(DD, NN) return apply_dn<T, DD, NN>(lv, pb, inv, invh, scale, res, jd, d, omega, omega_p, color, wstat, extra_tx, s)
+#define STMG_A(DD, NN) return apply_dn<T, DD, NN>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, wstat, extra_tx, s)
   if (lv.d == 2) { if (N == 3) STMG_A(2, 3); if (N == 4) STMG_A(2, 4); if (N == 5) STMG_A(2, 5); }
   else { if (N == 3) STMG_A(3, 3); if (N == 4) STMG_A(3, 4); }
 #undef STMG_A
@@ -220,10 +220,8 @@ template cudaError_t vanka_build<float>(const Level&, const Problem&, const floa
 template cudaError_t vanka_build<double>(const Level&, const Problem&, const double*, double*, double*, double*,
                                          double*, double*, void*, float*, int*, double*, cudaStream_t);
 template cudaError_t vanka_apply<float>(const Level&, const Problem&, const float*, const void*, const float*,
-                                        const float*, float*, double, double, int, int*, cudaStream_t, unsigned,
-                                        const float*);
+                                        const float*, float*, double, double, int, int*, cudaStream_t, unsigned);
 template cudaError_t vanka_apply<double>(const Level&, const Problem&, const double*, const void*, const float*,
-                                         const double*, double*, double, double, int, int*, cudaStream_t, unsigned,
-                                         const double*);
+                                         const double*, double*, double, double, int, int*, cudaStream_t, unsigned);
 
 }  // namespace stmg

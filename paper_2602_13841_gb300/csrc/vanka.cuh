@@ -580,8 +580,7 @@ __global__ void k_patch_global(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t c0
 }
 
 // ---------------------------------------------------------------------------- sweep
-// d[patch] += W~ S~^{-1} (res - jd)[patch] for the cells of one colour (jd = J d of the sweep, or null when
-// res already is the residual) (W~ = omega on velocity,
+// d[patch] += W~ S~^{-1} res[patch] for the cells of one colour (W~ = omega on velocity,
 // omega_p on pressure DoFs), through the time-diagonalised inverse (k_patch):
 //   rt_e = sum_a F[e][a] res_a  (per spatial patch DoF),  yhat_e = T_e^{-1} rt_e,
 //   y_a = sum_e Re(G[a][e] yhat_e).
@@ -656,9 +655,8 @@ __host__ __device__ inline size_t apply_slot_bytes(int kp1, int ms, size_t si, s
 
 template <typename T, typename SI, int D, int N>
 __global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const float* __restrict__ scale,
-                              const T* __restrict__ res, const T* __restrict__ jd, T* __restrict__ d, T omega,
-                              T omega_p, int kp1, int npc, TEig<T> te, ColorInfo ci, int* __restrict__ wstat,
-                              unsigned extra_tx) {
+                              const T* __restrict__ res, T* __restrict__ d, T omega, T omega_p, int kp1, int npc,
+                              TEig<T> te, ColorInfo ci, int* __restrict__ wstat, unsigned extra_tx) {
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int ms = MV + npc, st = inv_stride(ms), mr = (ms + 1) & ~1;
@@ -708,7 +706,7 @@ __global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const 
     gb[l] = g;
     T ra[MAXKP1];
 #pragma unroll
-    for (int a = 0; a < MAXKP1; ++a) ra[a] = a < kp1 ? res[g + a * sa] - (jd ? jd[g + a * sa] : (T)0) : (T)0;
+    for (int a = 0; a < MAXKP1; ++a) ra[a] = a < kp1 ? res[g + a * sa] : (T)0;
     for (int e = 0; e < te.nblk; ++e) {
       T fr = 0, fi = 0;
 #pragma unroll
@@ -781,8 +779,8 @@ template <> struct InvLdG<__half> {
 
 template <typename T, typename SI, int D, int N>
 __global__ void k_vanka_apply_global(LevelArgs<T> L, const SI* __restrict__ inv, const float* __restrict__ scale,
-                                     const T* __restrict__ res, const T* __restrict__ jd, T* __restrict__ d,
-                                     T omega, T omega_p, int kp1, int npc, TEig<T> te, ColorInfo ci) {
+                                     const T* __restrict__ res, T* __restrict__ d, T omega, T omega_p, int kp1,
+                                     int npc, TEig<T> te, ColorInfo ci) {
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int ms = MV + npc, st = inv_stride(ms), mr = (ms + 1) & ~1;
@@ -809,7 +807,7 @@ __global__ void k_vanka_apply_global(LevelArgs<T> L, const SI* __restrict__ inv,
     gb[l] = g;
     T ra[MAXKP1];
 #pragma unroll
-    for (int a = 0; a < MAXKP1; ++a) ra[a] = a < kp1 ? res[g + a * sa] - (jd ? jd[g + a * sa] : (T)0) : (T)0;
+    for (int a = 0; a < MAXKP1; ++a) ra[a] = a < kp1 ? res[g + a * sa] : (T)0;
     for (int e = 0; e < te.nblk; ++e) {
       T fr = 0, fi = 0;
 #pragma unroll
