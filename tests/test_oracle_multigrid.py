@@ -190,3 +190,35 @@ def test_vcycle_with_space_only_p_coarsening_contracts():
             x = x + mg.vcycle(b - J @ x)
         red[keep] = (np.linalg.norm(b - J @ x) / np.linalg.norm(b)) ** (1.0 / 6.0)
     assert red[True] < 0.6 and red[True] <= red[False] * 1.05, red
+
+
+def test_midpoint_surrogate_error_is_first_order_in_tau():
+    """Lemma (local Vanka surrogate, Sec. 4.3): with a state that varies smoothly in time,
+    ||S~ - S|| <= C tau with C proportional to ||M^tau||, so ||S~ - S|| / ||M^tau|| halves with
+    tau; and ||I - S^{-1} S~|| <= ||S^{-1}|| ||S~ - S|| (item (ii)).  S, S~: the space-time
+    patch matrices of one interior cell built from the exact Jacobian (convection at every time
+    node) and from the midpoint surrogate."""
+    from oracle import problems
+    from oracle.mesh import Mesh, Space
+    d, n, r, k, t0 = 2, 4, 1, 2, 0.7
+    verts = inputs.vertices(d, n, 0.1, 3)
+    prob = problems.make("MMS2D", 1e-2)
+    s = Space(Mesh(d, n, verts), r)
+    cell = 5                                                   # interior cell (1, 1)
+    ratios = []
+    for tau in (0.2, 0.1, 0.05, 0.025):
+        L = multigrid.Level(d, n, r, k, verts, tau, prob.nu, hscale=None)
+        times = L.td.times(t0)
+        U = np.concatenate([np.concatenate([forms.interpolate_velocity(s, lambda x, t=t: prob.v(x, t))
+                                            for t in times]), np.zeros((k + 1) * L.lay.Np)])
+        J = forms.jacobian(L.space, L.td, U, prob.nu)
+        Jt = forms.jacobian(L.space, L.td, U, prob.nu, vstar=multigrid.midpoint_velocity(L, U))
+        idx = multigrid.patch_dofs(L, cell)
+        S = J[idx][:, idx].toarray()
+        E = Jt[idx][:, idx].toarray() - S
+        nE = np.linalg.norm(E, 2)
+        ratios.append(nE / np.linalg.norm(L.td.M, 2))
+        lhs = np.linalg.norm(np.eye(len(idx)) - np.linalg.solve(S, S + E), 2)
+        assert lhs <= np.linalg.norm(np.linalg.inv(S), 2) * nE * (1 + 1e-12)
+    rates = [ratios[i] / ratios[i + 1] for i in range(len(ratios) - 1)]
+    assert all(1.8 < q < 2.2 for q in rates[1:]), (ratios, rates)
