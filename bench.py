@@ -187,6 +187,8 @@ def main():
     ap.add_argument("--smooth", type=int, default=0, help="Vanka pre- and post-sweeps per level (0: the workload's)")
     ap.add_argument("--keep-time-degree", type=int, default=0,
                     help="1: p-coarsen in space only, DG(k) on every level (a variant of the paper's order)")
+    ap.add_argument("--levels-h", type=int, default=-1,
+                    help="h-coarsenings below the p-levels (-1: down to 2 cells per direction)")
     ap.add_argument("--variant-smooth", type=int, default=2,
                     help="sweeps of the space-only p-coarsening variant timed beside the headline (0: skip)")
     ap.add_argument("--serving-requests", type=int, default=16,
@@ -219,7 +221,7 @@ def main():
                             problem=w["problem"], precond_precision=stmg.STMG_FP32, newton_rtol=w["rtol"],
                             newton_atol=w["atol"], vanka_fp16=int(args.vanka_fp16),
                             gmres_restart=w["restart"], gmres_maxit=w["restart"],
-                            keep_time_degree=int(args.keep_time_degree),
+                            keep_time_degree=int(args.keep_time_degree), n_levels_h=int(args.levels_h),
                             **dict(SMOOTH, nu1=args.smooth, nu2=args.smooth))
     stream = torch.cuda.Stream(device=dev)
     S = stmg.Solver(p, inputs.vertices(w["d"], w["n"], w["amp"], w["seed"]), stream=stream.cuda_stream)
