@@ -248,6 +248,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_volume2d(OpArgs
     u[c] = acc;
   }
   if (on && t < npc) pma = A.x[poff + (int64_t)a * L.Np + cell * npc + t];
+  // the output entries of this group (no other group of this colour writes them): read now, so
+  // that the update at the end is a plain store
+  T yold[2] = {0, 0}, pold = 0;
+  if (on) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) yold[c] = A.y[(int64_t)a * L.Nv + c * L.nnodes + gnode];
+    if (t < npc) pold = A.y[poff + (int64_t)a * L.Np + cell * npc + t];
+  }
   // corners and geometry at quadrature point t: read from the precomputed table for the Jacobian
   // apply (the corners then only serve the boundary faces), else computed from the vertices
   const bool bcell = on && (cc[0] == 0 || cc[1] == 0 || cc[0] == L.n - 1 || cc[1] == L.n - 1);
@@ -370,9 +378,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_volume2d(OpArgs
   }
   if (on) {
 #pragma unroll
-    for (int c = 0; c < 2; ++c) A.y[(int64_t)a * L.Nv + c * L.nnodes + gnode] += vout[c];
+    for (int c = 0; c < 2; ++c) A.y[(int64_t)a * L.Nv + c * L.nnodes + gnode] = yold[c] + vout[c];
   }
-  if (on && t < npc) A.y[poff + (int64_t)a * L.Np + cell * npc + t] += pacc;
+  if (on && t < npc) A.y[poff + (int64_t)a * L.Np + cell * npc + t] = pold + pacc;
 }
 
 // Geometry table of a 2D level for k_volume2d: per cell and Gauss point t the inverse Jacobian
