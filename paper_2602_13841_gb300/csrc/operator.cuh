@@ -156,6 +156,20 @@ __global__ void k_volume(OpArgs<T> A, Tab<T> tb_p, ColorInfo ci, int cpb) {
     if (t < npc)
       for (int b = 0; b < kp1; ++b) s_pm[b * MAXNP + t] = A.x[poff + (int64_t)b * L.Np + cell * npc + t];
   }
+  // the output entries of lane t (node t, pressure mode t; no other block of this colour writes
+  // them): read with the inputs, so that each time node's update is a plain store
+  T yo[MAXKP1][3], po[MAXKP1];
+#pragma unroll
+  for (int a = 0; a < MAXKP1; ++a) {
+    po[a] = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) yo[a][c] = 0;
+    if (on && a < kp1) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) yo[a][c] = A.y[(int64_t)a * L.Nv + c * L.nnodes + gnode];
+      if (t < npc) po[a] = A.y[poff + (int64_t)a * L.Np + cell * npc + t];
+    }
+  }
   __syncthreads();
   tensor_pass<T, D, N, false>(s_val, s_tmp, tb.B, t, kp1 * D, on);
   if (MODE == MJ) tensor_pass<T, D, N, false>(s_st, s_tmp, tb.B, t, kp1 * D, on);
@@ -266,7 +280,15 @@ __global__ void k_volume(OpArgs<T> A, Tab<T> tb_p, ColorInfo ci, int cpb) {
     __syncthreads();
     tensor_pass<T, D, N, true>(s_z2, s_z, tb.B, t, D, on);
     if (on) {
-      for (int c = 0; c < D; ++c) A.y[(int64_t)a * L.Nv + c * L.nnodes + gnode] += s_z2[c * Q + t];
+      T ya[3] = {0, 0, 0}, pa = 0;
+#pragma unroll
+      for (int q = 0; q < MAXKP1; ++q)
+        if (q == a) {
+          pa = po[q];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) ya[c] = yo[q][c];
+        }
+      for (int c = 0; c < D; ++c) A.y[(int64_t)a * L.Nv + c * L.nnodes + gnode] = ya[c] + s_z2[c * Q + t];
       if (t < npc) {
         T acc = 0;
         for (int q = 0; q < Q; ++q) {
@@ -275,7 +297,7 @@ __global__ void k_volume(OpArgs<T> A, Tab<T> tb_p, ColorInfo ci, int cpb) {
           if (D == 3) psi *= tb.P1[q2][tb.modes[t][2]];
           acc += psi * s_sp[q];
         }
-        A.y[poff + (int64_t)a * L.Np + cell * npc + t] += acc;
+        A.y[poff + (int64_t)a * L.Np + cell * npc + t] = pa + acc;
       }
     }
     __syncthreads();
@@ -387,6 +409,11 @@ __global__ void k_faces(OpArgs<T> A, Tab<T> tb_p, const int* __restrict__ bcells
   if (on && t == 0) { T v = 0; for (int q = 0; q < Q; ++q) v += s_red[q]; s_sc[0] = v; }
   __syncthreads();
 
+  // the faces of a cell add to the same entries of y (lane t: node t, pressure mode t): sum them
+  // in registers and update y once after the face loop
+  T ysum[MAXKP1][3], psum[MAXKP1];
+#pragma unroll
+  for (int a = 0; a < MAXKP1; ++a) { psum[a] = 0; for (int c = 0; c < 3; ++c) ysum[a][c] = 0; }
   for (int axis = 0; axis < D; ++axis)
     for (int side = 0; side < 2; ++side) {
       // uniform across the block: every group runs the loop; groups whose cell does not have
@@ -482,19 +509,32 @@ __global__ void k_faces(OpArgs<T> A, Tab<T> tb_p, const int* __restrict__ bcells
               out[c] += acc;
             }
           }
-          for (int c = 0; c < D; ++c) A.y[(int64_t)a * L.Nv + c * L.nnodes + gnode] += out[c];
+#pragma unroll
+          for (int q = 0; q < MAXKP1; ++q)
+            if (q == a)
+              for (int c = 0; c < D; ++c) ysum[q][c] += out[c];
           if (t < npc) {
             T acc = 0;
             for (int p = 0; p < NF; ++p) {
               int pp[2] = {p % N, p / N};
               acc += s_s[p] * face_psi<T, D, N>(tb, axis, side, pp, t);
             }
-            A.y[poff + (int64_t)a * L.Np + cell * npc + t] += acc;
+#pragma unroll
+            for (int q = 0; q < MAXKP1; ++q)
+              if (q == a) psum[q] += acc;
           }
         }
         __syncthreads();
       }
     }
+  if (on) {
+#pragma unroll
+    for (int a = 0; a < MAXKP1; ++a) {
+      if (a < a_lo || a >= a_hi) continue;
+      for (int c = 0; c < D; ++c) A.y[(int64_t)a * L.Nv + c * L.nnodes + gnode] += ysum[a][c];
+      if (t < npc) A.y[poff + (int64_t)a * L.Np + cell * npc + t] += psum[a];
+    }
+  }
 }
 
 }  // namespace stmg

@@ -805,6 +805,11 @@ __global__ void k_vanka_apply_global(LevelArgs<T> L, const SI* __restrict__ inv,
   decode_color_cell<D>(ci, cidx, cc);
   int64_t cell = 0, s = 1;
   for (int l = 0; l < D; ++l) { cell += (int64_t)cc[l] * s; s *= L.n; }
+  // each thread also reads the current correction on its own row (no other block of this
+  // colour touches these entries), so the update at the end is a plain store
+  T dold[MAXKP1];
+#pragma unroll
+  for (int a = 0; a < MAXKP1; ++a) dold[a] = 0;
   for (int l = tid; l < ms; l += nt) {
     int64_t g, sa;
     if (l < MV) {
@@ -819,6 +824,10 @@ __global__ void k_vanka_apply_global(LevelArgs<T> L, const SI* __restrict__ inv,
     T ra[MAXKP1];
 #pragma unroll
     for (int a = 0; a < MAXKP1; ++a) ra[a] = a < kp1 ? res[g + a * sa] : (T)0;
+    if (l == tid) {
+#pragma unroll
+      for (int a = 0; a < MAXKP1; ++a) dold[a] = a < kp1 ? d[g + a * sa] : (T)0;
+    }
     for (int e = 0; e < te.nblk; ++e) {
       T fr = 0, fi = 0;
 #pragma unroll
@@ -857,12 +866,14 @@ __global__ void k_vanka_apply_global(LevelArgs<T> L, const SI* __restrict__ inv,
   const int64_t g = gb[i];
   const int64_t sa = i < MV ? L.Nv : L.Np;
   const T wgt = i < MV ? omega : omega_p;
-  for (int a = 0; a < kp1; ++a) {
+#pragma unroll
+  for (int a = 0; a < MAXKP1; ++a) {
+    if (a >= kp1) break;
     T y = 0;
 #pragma unroll
     for (int e = 0; e < MAXKP1; ++e)
       if (e < te.nblk) y += te.Gre[a][e] * yr[e] - te.Gim[a][e] * yi[e];
-    d[g + a * sa] += wgt * y;
+    d[g + a * sa] = dold[a] + wgt * y;
   }
 }
 
