@@ -167,7 +167,6 @@ cudaError_t coarse_invert(const double* A, float* Ainv, float* col, int* piv, in
 
 template <typename TA>
 __global__ void k_gemv_cm(const TA* __restrict__ A, int n, const double* __restrict__ x, double* __restrict__ y) {
-  pdl_enter();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double acc = 0.0;
     for (int j = 0; j < n; ++j) acc += (double)A[(int64_t)j * n + i] * x[j];
@@ -176,15 +175,15 @@ __global__ void k_gemv_cm(const TA* __restrict__ A, int n, const double* __restr
 }
 
 cudaError_t gemv_cm(const double* A, int n, const double* x, double* y, cudaStream_t s) {
-  cudaError_t e = launch_pdl(k_gemv_cm<double>, dim3((n + 127) / 128), dim3(128), 0, s, A, n, x, y);
+  k_gemv_cm<double><<<(n + 127) / 128, 128, 0, s>>>(A, n, x, y);
   note_launch();
-  return e;
+  return cudaGetLastError();
 }
 
 cudaError_t gemv_cm(const float* A, int n, const double* x, double* y, cudaStream_t s) {
-  cudaError_t e = launch_pdl(k_gemv_cm<float>, dim3((n + 127) / 128), dim3(128), 0, s, A, n, x, y);
+  k_gemv_cm<float><<<(n + 127) / 128, 128, 0, s>>>(A, n, x, y);
   note_launch();
-  return e;
+  return cudaGetLastError();
 }
 
 }  // namespace stmg

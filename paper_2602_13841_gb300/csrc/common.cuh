@@ -4,7 +4,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "pdl.cuh"
 #include "refdata.hpp"
 
 namespace stmg {

@@ -129,7 +129,7 @@ cudaError_t MG<T>::setup(const double* U64) {
 template <typename T>
 cudaError_t MG<T>::coarse_solve(const T* rhs, T* d) {
   cudaStream_t s = h->stream;
-  CKE(vfill<double>(Nb, 0.0, cb, s));
+  CKE(cudaMemsetAsync(cb, 0, Nb * sizeof(double), s));
   CKE((vcopy<T, double>(Nc, rhs, cb, s)));
   CKE(gemv_cm(Ainv, Nb, cb, cx, s));
   for (int it = 0; it < 3; ++it) {          // FP64 iterative refinement
@@ -151,7 +151,7 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
   for (int it = 0; it < nsweeps; ++it) {
     const T* res = rhs;
     if (it == 0 && zero_start) {
-      CKE(vfill<T>(lv.Nst, (T)0, d, s));
+      CKE(cudaMemsetAsync(d, 0, lv.Nst * sizeof(T), s));
     } else {
       // q = rhs - J d
       h->kbegin(KC_APPLYP);
@@ -187,7 +187,7 @@ cudaError_t MG<T>::vcycle_level(int l, const T* rhs, T* d) {
   const Level& lv = h->levels[l];
   const int nu1 = h->prm.nu1 > 0 ? h->prm.nu1 : 0, nu2 = h->prm.nu2 > 0 ? h->prm.nu2 : 0;
   if (nu1 > 0) CKE(sweep(l, rhs, d, nu1, true));
-  else CKE(vfill<T>(lv.Nst, (T)0, d, s));
+  else CKE(cudaMemsetAsync(d, 0, lv.Nst * sizeof(T), s));
   // t = rhs - J d ; r_{l+1} = P^T t
   h->kbegin(KC_APPLYP);
   CKE(launch_operator<T>(lv, h->pb, OP_JAC, 0.0, d, U[l], nullptr, t[l], s));

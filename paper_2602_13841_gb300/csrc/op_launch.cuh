@@ -5,7 +5,6 @@
 #include "operator.cuh"
 #include "operator2d.cuh"
 #include "counters.hpp"
-#include "vec.cuh"
 
 namespace stmg {
 
@@ -62,7 +61,7 @@ static cudaError_t launch_dn(const Level& lv, const Problem& pb, double t0, cons
     if (e != cudaSuccess) return e;
   }
   for (int b = 0; b < batch; ++b) {
-    e = vfill<T>(lv.Nst, (T)0, y + b * ys, stream);       // a kernel, so the colour launches chain by PDL
+    e = cudaMemsetAsync(y + b * ys, 0, sizeof(T) * lv.Nst, stream);
     if (e != cudaSuccess) return e;
   }
   for (int c = 0; c < lv.ncolors; ++c) {
@@ -73,21 +72,17 @@ static cudaError_t launch_dn(const Level& lv, const Problem& pb, double t0, cons
         constexpr int cpw = 32 / Q, per_block = 8 * cpw;
         const int64_t groups = (int64_t)ci.count * kp1;
         dim3 grid((unsigned)((groups + per_block - 1) / per_block), batch);
-        e = launch_pdl(k_volume2d<T, N, MODE>, grid, dim3(256), 0, stream, A, tb, ci);
-        if (e != cudaSuccess) return e;
+        k_volume2d<T, N, MODE><<<grid, 256, 0, stream>>>(A, tb, ci);
       } else {
         dim3 grid((ci.count + cpb - 1) / cpb, batch);
-        e = launch_pdl(k_volume<T, D, N, MODE>, grid, dim3(cpb * Q), (size_t)smem, stream, A, tb, ci, cpb);
-        if (e != cudaSuccess) return e;
+        k_volume<T, D, N, MODE><<<grid, cpb * Q, smem, stream>>>(A, tb, ci, cpb);
       }
       note_launch();
     }
     if (D == 3 && MODE != MM && lv.nbcells[c] > 0) {       // 2D: faces fused into k_volume2d
       // one block per (boundary cell, time node) when fcpb == 1
       dim3 grid(fcpb == 1 ? lv.nbcells[c] * kp1 : (lv.nbcells[c] + fcpb - 1) / fcpb, batch);
-      e = launch_pdl(k_faces<T, D, N, MODE>, grid, dim3(fcpb * Q), (size_t)fsmem, stream, A, tb,
-                     (const int*)lv.bcells[c], (int)lv.nbcells[c], fcpb);
-      if (e != cudaSuccess) return e;
+      k_faces<T, D, N, MODE><<<grid, fcpb * Q, fsmem, stream>>>(A, tb, lv.bcells[c], lv.nbcells[c], fcpb);
       note_launch();
     }
   }

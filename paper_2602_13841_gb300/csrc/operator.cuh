@@ -112,7 +112,6 @@ enum { MJ = 0, MR = 1, MM = 2 };   // Jacobian apply, residual, mass (w_a M_h, w
 
 template <typename T, int D, int N, int MODE>
 __global__ void k_volume(OpArgs<T> A, Tab<T> tb_p, ColorInfo ci, int cpb) {
-  pdl_enter();
   __shared__ __align__(16) unsigned char s_tab[sizeof(Tab<T>)];
   const Tab<T>& tb = stage_tab(tb_p, s_tab);
   constexpr bool RES = (MODE == MR);
@@ -347,7 +346,6 @@ __device__ inline T face_psi(const Tab<T>& tb, int axis, int side, const int* pq
 
 template <typename T, int D, int N, int MODE>
 __global__ void k_faces(OpArgs<T> A, Tab<T> tb_p, const int* __restrict__ bcells, int nb, int cpb) {
-  pdl_enter();
   __shared__ __align__(16) unsigned char s_tab[sizeof(Tab<T>)];
   const Tab<T>& tb = stage_tab(tb_p, s_tab);
   constexpr int Q = Shape<D, N>::Q;

@@ -193,7 +193,6 @@ __device__ __forceinline__ void face2d(const OpArgs<T>& A, const Tab<T>& tb, int
 
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_volume2d(OpArgs<T> A, Tab<T> tb, ColorInfo ci) {
-  pdl_enter();
   constexpr int Q = N * N;
   constexpr int CPW = 32 / Q;                       // (cell, time node) groups per warp
   constexpr bool RES = (MODE == MR);

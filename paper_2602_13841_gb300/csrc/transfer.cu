@@ -5,7 +5,6 @@
 #include "handle.hpp"
 #include "transfer.hpp"
 #include "counters.hpp"
-#include "pdl.cuh"
 
 namespace stmg {
 
@@ -131,7 +130,6 @@ template <typename T>
 __global__ void k_axis(const T* __restrict__ in, T* __restrict__ out, int nin, int nout, int64_t inner,
                        int64_t outer, int64_t sin, int64_t sout, const int* __restrict__ rowptr,
                        const int* __restrict__ col, const T* __restrict__ val) {
-  pdl_enter();
   const int b = blockIdx.y;
   const int64_t total = outer * nout * inner;
   in += b * sin;
@@ -153,7 +151,6 @@ struct Mat3 { double m[MAXKP1][MAXKP1]; };
 template <typename T>
 __global__ void k_timemix(const T* __restrict__ in, T* __restrict__ out, int64_t L, int nin, int nout,
                           int64_t sin, int64_t sout, Mat3 M) {
-  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x) {
     T v[MAXKP1];
     for (int a = 0; a < nin; ++a) v[a] = in[a * sin + i];
@@ -169,7 +166,6 @@ __global__ void k_timemix(const T* __restrict__ in, T* __restrict__ out, int64_t
 template <typename T, int D>
 __global__ void k_pprolong(const T* __restrict__ in, T* __restrict__ out, int nf, int ratio, int npf, int npc,
                            const T* __restrict__ PT, int64_t sin, int64_t sout) {
-  pdl_enter();
   const int b = blockIdx.y;
   in += b * sin; out += b * sout;
   int64_t ncf = 1;
@@ -196,7 +192,6 @@ __global__ void k_pprolong(const T* __restrict__ in, T* __restrict__ out, int nf
 template <typename T, int D>
 __global__ void k_prestrict(const T* __restrict__ in, T* __restrict__ out, int nf, int ratio, int npf, int npc,
                             const T* __restrict__ PT, int64_t sin, int64_t sout) {
-  pdl_enter();
   const int b = blockIdx.y;
   in += b * sin; out += b * sout;
   const int nc = nf / ratio;
@@ -253,10 +248,8 @@ static cudaError_t tensor_apply(const Csr1D& op, int d, int nin, int nout, int b
     // the final pass writes with the caller's stride (= nout^d)
     if (ax == d - 1) sdst = sout;
     dim3 grid(grid1(outer * nout * inner), batch);
-    cudaError_t e = launch_pdl(k_axis<T>, grid, dim3(256), 0, s, src, dst, (int)ext[ax], nout, inner, outer, sin, sdst,
-                               op.rowptr, op.col, vals<T>(op));
+    k_axis<T><<<grid, 256, 0, s>>>(src, dst, (int)ext[ax], nout, inner, outer, sin, sdst, op.rowptr, op.col, vals<T>(op));
     note_launch();
-    if (e != cudaSuccess) return e;
     ext[ax] = nout;
     src = dst;
     sin = sdst;
@@ -274,21 +267,19 @@ cudaError_t Transfer::prolong(const T* xc, T* xf, cudaStream_t s) const {
   if (e != cudaSuccess) return e;
   Mat3 M{};
   for (int a = 0; a <= f.k; ++a) for (int b = 0; b <= c.k; ++b) M.m[a][b] = E[a][b];
-  e = launch_pdl(k_timemix<T>, dim3(grid1(f.Nv)), dim3(256), 0, s, (const T*)C, xf, f.Nv, c.k + 1, f.k + 1, f.Nv, f.Nv, M);
+  k_timemix<T><<<grid1(f.Nv), 256, 0, s>>>(C, xf, f.Nv, c.k + 1, f.k + 1, f.Nv, f.Nv, M);
   note_launch();
-  if (e != cudaSuccess) return e;
   // pressure
   const T* pc = xc + (int64_t)(c.k + 1) * c.Nv;
   T* pf = xf + (int64_t)(f.k + 1) * f.Nv;
   int64_t ncf = f.Np / f.npc;
   dim3 g(grid1(ncf * f.npc), c.k + 1);
-  e = d == 2 ? launch_pdl(k_pprolong<T, 2>, g, dim3(256), 0, s, pc, C, f.n, ratio, f.npc, c.npc, ptab<T>(*this), c.Np, f.Np)
-             : launch_pdl(k_pprolong<T, 3>, g, dim3(256), 0, s, pc, C, f.n, ratio, f.npc, c.npc, ptab<T>(*this), c.Np, f.Np);
+  if (d == 2) k_pprolong<T, 2><<<g, 256, 0, s>>>(pc, C, f.n, ratio, f.npc, c.npc, ptab<T>(*this), c.Np, f.Np);
+  else k_pprolong<T, 3><<<g, 256, 0, s>>>(pc, C, f.n, ratio, f.npc, c.npc, ptab<T>(*this), c.Np, f.Np);
   note_launch();
-  if (e != cudaSuccess) return e;
-  e = launch_pdl(k_timemix<T>, dim3(grid1(f.Np)), dim3(256), 0, s, (const T*)C, pf, f.Np, c.k + 1, f.k + 1, f.Np, f.Np, M);
+  k_timemix<T><<<grid1(f.Np), 256, 0, s>>>(C, pf, f.Np, c.k + 1, f.k + 1, f.Np, f.Np, M);
   note_launch();
-  return e;
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -298,22 +289,20 @@ cudaError_t Transfer::restrict_(const T* xf, T* xc, cudaStream_t s) const {
   const int d = f.d;
   Mat3 M{};
   for (int a = 0; a <= c.k; ++a) for (int b = 0; b <= f.k; ++b) M.m[a][b] = E[b][a];   // E^T
-  cudaError_t e = launch_pdl(k_timemix<T>, dim3(grid1(f.Nv)), dim3(256), 0, s, xf, C, f.Nv, f.k + 1, c.k + 1, f.Nv, f.Nv, M);
+  k_timemix<T><<<grid1(f.Nv), 256, 0, s>>>(xf, C, f.Nv, f.k + 1, c.k + 1, f.Nv, f.Nv, M);
   note_launch();
-  if (e != cudaSuccess) return e;
-  e = tensor_apply<T>(P1T, d, f.N1, c.N1, (c.k + 1) * d, C, xc, A, B, s);
+  cudaError_t e = tensor_apply<T>(P1T, d, f.N1, c.N1, (c.k + 1) * d, C, xc, A, B, s);
   if (e != cudaSuccess) return e;
   const T* pf = xf + (int64_t)(f.k + 1) * f.Nv;
   T* pc = xc + (int64_t)(c.k + 1) * c.Nv;
-  e = launch_pdl(k_timemix<T>, dim3(grid1(f.Np)), dim3(256), 0, s, pf, C, f.Np, f.k + 1, c.k + 1, f.Np, f.Np, M);
+  k_timemix<T><<<grid1(f.Np), 256, 0, s>>>(pf, C, f.Np, f.k + 1, c.k + 1, f.Np, f.Np, M);
   note_launch();
-  if (e != cudaSuccess) return e;
   int64_t ncc = c.Np / c.npc;
   dim3 g(grid1(ncc * c.npc), c.k + 1);
-  e = d == 2 ? launch_pdl(k_prestrict<T, 2>, g, dim3(256), 0, s, (const T*)C, pc, f.n, ratio, f.npc, c.npc, ptab<T>(*this), f.Np, c.Np)
-             : launch_pdl(k_prestrict<T, 3>, g, dim3(256), 0, s, (const T*)C, pc, f.n, ratio, f.npc, c.npc, ptab<T>(*this), f.Np, c.Np);
+  if (d == 2) k_prestrict<T, 2><<<g, 256, 0, s>>>(C, pc, f.n, ratio, f.npc, c.npc, ptab<T>(*this), f.Np, c.Np);
+  else k_prestrict<T, 3><<<g, 256, 0, s>>>(C, pc, f.n, ratio, f.npc, c.npc, ptab<T>(*this), f.Np, c.Np);
   note_launch();
-  return e;
+  return cudaGetLastError();
 }
 
 template <typename T>

@@ -164,9 +164,10 @@ static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv
   if (!apply_onchip(lv, sizeof(SI), sizeof(T))) {
     const int mr = (ms + 1) & ~1;
     const size_t gsm = (((size_t)kp1 * mr * sizeof(T) + 7) & ~(size_t)7) + (size_t)ms * 8;
-    return launch_pdl(k_vanka_apply_global<T, SI, D, N>, dim3((unsigned)ci.count), dim3(threads), gsm, s,
-                      level_args<T>(lv, pb, 0.0), inv, scale, res, d, (T)omega, (T)omega_p, kp1, lv.npc,
-                      make_teig<T>(lv.tabs, pb.tau), ci);
+    k_vanka_apply_global<T, SI, D, N><<<(unsigned)ci.count, threads, gsm, s>>>(
+        level_args<T>(lv, pb, 0.0), inv, scale, res, d, (T)omega, (T)omega_p, kp1, lv.npc,
+        make_teig<T>(lv.tabs, pb.tau), ci);
+    return cudaSuccess;
   }
   // cells per block: 4 for one-warp patches (32 resident blocks per SM), else 1
   const size_t slot = apply_slot_bytes(kp1, ms, sizeof(SI), sizeof(T));
@@ -176,9 +177,10 @@ static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv
   cudaError_t e = allow_smem(k_vanka_apply<T, SI, D, N>, smem);
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((ci.count + cpb - 1) / cpb);
-  return launch_pdl(k_vanka_apply<T, SI, D, N>, dim3(blocks), dim3(threads * cpb), smem, s, level_args<T>(lv, pb, 0.0),
-                    inv, scale, res, d, (T)omega, (T)omega_p, kp1, lv.npc, make_teig<T>(lv.tabs, pb.tau), ci, wstat,
-                    extra_tx);
+  k_vanka_apply<T, SI, D, N><<<blocks, threads * cpb, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, scale, res, d,
+                                                                       (T)omega, (T)omega_p, kp1, lv.npc,
+                                                                       make_teig<T>(lv.tabs, pb.tau), ci, wstat, extra_tx);
+  return cudaSuccess;
 }
 
 template <typename T, int D, int N>

@@ -657,7 +657,6 @@ template <typename T, typename SI, int D, int N>
 __global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const float* __restrict__ scale,
                               const T* __restrict__ res, T* __restrict__ d, T omega, T omega_p, int kp1, int npc,
                               TEig<T> te, ColorInfo ci, int* __restrict__ wstat, unsigned extra_tx) {
-  pdl_enter();
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int ms = MV + npc, st = inv_stride(ms), mr = (ms + 1) & ~1;
@@ -793,7 +792,6 @@ template <typename T, typename SI, int D, int N>
 __global__ void k_vanka_apply_global(LevelArgs<T> L, const SI* __restrict__ inv, const float* __restrict__ scale,
                                      const T* __restrict__ res, T* __restrict__ d, T omega, T omega_p, int kp1,
                                      int npc, TEig<T> te, ColorInfo ci) {
-  pdl_enter();
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int ms = MV + npc, st = inv_stride(ms), mr = (ms + 1) & ~1;

@@ -1,7 +1,6 @@
 // Vector kernels (see vec.cuh).  Grid-stride loops sized as a multiple of the SM count;
 // reductions in a fixed order (block partial sums, then one block per result).
 #include "vec.cuh"
-#include "pdl.cuh"
 #include "counters.hpp"
 
 namespace stmg {
@@ -15,30 +14,28 @@ static inline int grid_for(int64_t n) {
 
 template <typename T>
 __global__ void k_axpby(int64_t n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
-  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i] + b * y[i];
 }
 
 template <typename T>
 cudaError_t vaxpby(int64_t n, T a, const T* x, T b, T* y, cudaStream_t s) {
-  cudaError_t e = launch_pdl(k_axpby<T>, dim3(grid_for(n)), dim3(256), 0, s, n, a, x, b, y);
+  k_axpby<T><<<grid_for(n), 256, 0, s>>>(n, a, x, b, y);
   note_launch();
-  return e;
+  return cudaGetLastError();
 }
 
 template <typename S, typename T>
 __global__ void k_copy(int64_t n, const S* __restrict__ x, T* __restrict__ y) {
-  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (T)x[i];
 }
 
 template <typename S, typename T>
 cudaError_t vcopy(int64_t n, const S* x, T* y, cudaStream_t s) {
-  cudaError_t e = launch_pdl(k_copy<S, T>, dim3(grid_for(n)), dim3(256), 0, s, n, x, y);
+  k_copy<S, T><<<grid_for(n), 256, 0, s>>>(n, x, y);
   note_launch();
-  return e;
+  return cudaGetLastError();
 }
 
 // Partial dot products of up to DOTS_PER_ROW basis vectors with w per block: w[i] is read once
@@ -173,15 +170,14 @@ cudaError_t vscale(int64_t n, T a, const T* x, T* y, cudaStream_t s) {
 
 template <typename T>
 __global__ void k_fill(int64_t n, T v, T* __restrict__ x) {
-  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = v;
 }
 
 template <typename T>
 cudaError_t vfill(int64_t n, T v, T* x, cudaStream_t s) {
-  cudaError_t e = launch_pdl(k_fill<T>, dim3(grid_for(n)), dim3(256), 0, s, n, v, x);
+  k_fill<T><<<grid_for(n), 256, 0, s>>>(n, v, x);
   note_launch();
-  return e;
+  return cudaGetLastError();
 }
 
 __global__ void k_finite(int64_t n, const double* __restrict__ x, int* flag) {
