@@ -13,6 +13,8 @@
 namespace stmg {
 
 constexpr int MAXNP2D = 10;   // C(r+2, 2) for r <= 3
+// pressure modes of P_r on a level whose velocity has N = r + 2 nodes per direction: C(r+2, 2)
+template <int N> __host__ __device__ constexpr int np2d() { return N * (N - 1) / 2; }
 
 template <typename T, int N>
 __device__ __forceinline__ T shfl_x(T v, const T (*M)[MAXN], int row, int base, bool transpose) {
@@ -97,13 +99,11 @@ __device__ __forceinline__ void face2d(const OpArgs<T>& A, const Tab<T>& tb, int
   // pressure at face point tt: psi_m(face point) = Pend[side][m_axis] P1[tt][m_other]
   T fp = 0;
 #pragma unroll
-  for (int m = 0; m < MAXNP2D; ++m) {
-    if (m < npc) {
-      const T pm = __shfl_sync(0xffffffffu, pma, cb + m);
-      const T psi = (axis == 0) ? tb.Pend[side][tb.modes[m][0]] * tb.P1[tt][tb.modes[m][1]]
-                                : tb.P1[tt][tb.modes[m][0]] * tb.Pend[side][tb.modes[m][1]];
-      fp += psi * pm;
-    }
+  for (int m = 0; m < np2d<N>(); ++m) {
+    const T pm = __shfl_sync(0xffffffffu, pma, cb + m);
+    const T psi = (axis == 0) ? tb.Pend[side][tb.modes[m][0]] * tb.P1[tt][tb.modes[m][1]]
+                              : tb.P1[tt][tb.modes[m][0]] * tb.Pend[side][tb.modes[m][1]];
+    fp += psi * pm;
   }
   // geometry at the face point
   T xh[3], J[3][3], G[3][3], xf[3];
@@ -305,9 +305,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_volume2d(OpArgs
   // pressure at this quadrature point
   T pq = 0;
 #pragma unroll
-  for (int m = 0; m < MAXNP2D; ++m) {
-    const T pm = __shfl_sync(0xffffffffu, pma, cb + (m < Q ? m : 0));
-    if (m < npc) pq += sP1[tx][tb.modes[m][0]] * sP1[ty][tb.modes[m][1]] * pm;
+  for (int m = 0; m < np2d<N>(); ++m) {
+    const T pm = __shfl_sync(0xffffffffu, pma, cb + m);
+    pq += sP1[tx][tb.modes[m][0]] * sP1[ty][tb.modes[m][1]] * pm;
   }
   // reference gradients by the collocation derivative of the Gauss-point values
   T gref[2][2];
@@ -357,15 +357,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_volume2d(OpArgs
     T v = shfl_x<T, N>(z[c], sB, tx, cb + ty * N, true);
     vout[c] = shfl_y<T, N>(v, sB, ty, cb + tx, true);
   }
-  // pressure test functions: lane cb + m accumulates sum_t psi_m(t) sp(t)
-  T pacc = 0;
-  const int mo = t < npc ? t : 0;
-  const int mx = tb.modes[mo][0], my = tb.modes[mo][1];
+  // pressure test functions, sum_t psi_m(t) sp(t) with psi_m = P_mx(x) P_my(y), factorised:
+  // lane (i, j) forms sum_qx P_i(qx) sp(qx, j), then sum_qy P_j(qy) of those along y; lane cb + m
+  // takes the value of lane (mx, my).  Degrees run to r = N - 2; lanes i or j = N - 1 compute
+  // an unused value (index clamped to a valid column of the table).
+  const int dx = tx < N - 1 ? tx : 0, dy = ty < N - 1 ? ty : 0;
+  T s1 = 0;
 #pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    T sv = __shfl_sync(0xffffffffu, sp, cb + q);
-    pacc += sP1[q % N][mx] * sP1[q / N][my] * sv;
-  }
+  for (int j = 0; j < N; ++j) s1 += sP1[j][dx] * __shfl_sync(0xffffffffu, sp, cb + ty * N + j);
+  T s2 = 0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) s2 += sP1[j][dy] * __shfl_sync(0xffffffffu, s1, cb + tx + j * N);
+  const int mo = t < npc ? t : 0;
+  T pacc = __shfl_sync(0xffffffffu, s2, cb + tb.modes[mo][0] + N * tb.modes[mo][1]);
   // boundary faces (Nitsche, boundary convection) of boundary cells
   if (MODE != MM) {
 #pragma unroll
