@@ -30,6 +30,12 @@ import sys
 import threading
 import time
 
+# The oracle timing (the reference arm, and the cpu_baseline leg run in a child process) uses one
+# BLAS / OpenMP thread, so that `cores` states the threads it actually used.
+if "--oracle-child" in sys.argv or ("--impl" in sys.argv and "reference" in sys.argv):
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        os.environ[_v] = "1"
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -121,7 +127,31 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def _cpu_cores():
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_child(n, smooth, workload):
+    """Time the oracle sample in a child process (fresh interpreter, one BLAS thread): returns
+    the cpu_baseline object."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-child", "--workload", workload,
+           "--ref-n", str(n), "--smooth", str(smooth)]
+    res = subprocess.run(cmd, capture_output=True, text=True, timeout=1800)
+    if res.returncode != 0:
+        return {"value": None, "unit": "DoF/s", "kind": "oracle", "error": res.stderr.strip()[-300:]}
+    v, desc = json.loads(res.stdout.strip().splitlines()[-1])
+    return {"value": v, "unit": "DoF/s", "cores": 1, "cpu_model": _cpu_model(), "host_cores": _host_cores(),
+            "kind": "oracle", "sample": desc}
+
+
+def _host_cores():
     try:
         return len(os.sched_getaffinity(0))
     except Exception:
@@ -170,8 +200,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": W["name"], "sample": desc},
-            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": _cpu_cores(), "kind": "oracle",
-                             "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "cpu_model": _cpu_model(),
+                             "host_cores": _host_cores(), "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -201,8 +231,13 @@ def main():
                     help="sweeps of the space-only p-coarsening variant timed beside the headline (0: skip)")
     ap.add_argument("--serving-requests", type=int, default=16,
                     help="requests of the serving leg (Poisson stream, 20/s); 0 skips it")
+    ap.add_argument("--oracle-child", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     W = WORKLOADS[args.workload]
+    if args.oracle_child:
+        v, dt, nst, desc = oracle_sample(n=args.ref_n or W["oracle_n"], smooth=args.smooth or W["smooth"], w=W)
+        print(json.dumps([v, desc]), flush=True)
+        return
     if args.n <= 0:
         args.n = W["n"]
     if args.smooth <= 0:
@@ -394,8 +429,7 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            v, dt, nst, desc = oracle_sample(n=W["oracle_n"], smooth=args.smooth, w=W)
-            cpu = {"value": v, "unit": "DoF/s", "cores": _cpu_cores(), "kind": "oracle", "sample": desc}
+            cpu = oracle_child(W["oracle_n"], args.smooth, args.workload)
         line = {
             "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
