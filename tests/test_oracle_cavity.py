@@ -97,3 +97,11 @@ def test_slab_solution_is_mirror_symmetric_in_y():
     scale = np.abs(X[:nv]).max()
     assert scale > 0.05                                          # the lid drives a flow
     assert np.abs(W - X).max() < 1e-9 * max(scale, np.abs(X[nv:]).max())
+
+
+def test_space_time_size_matches_the_papers_table():
+    """Table st-sizes, c = 4, r = 2: 16^3 cells, 256 slabs of DG(2) on [0, 8], Q3/P2disc --
+    302 520 576 space-time unknowns; the oracle's slab layout times the number of slabs."""
+    s = Space(Mesh(3, 16, uniform_vertices(3, 16)), 2)
+    lay = forms.SlabLayout(s, 2)
+    assert 256 * lay.Nst == 302520576
