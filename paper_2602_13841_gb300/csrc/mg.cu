@@ -30,10 +30,10 @@ cudaError_t MG<T>::allocate(Handle* hh) {
         if (!vanka_supported(lv, sizeof(T))) { smoothable = false; continue; }
         size_t m = vanka_patch_size(lv);
         if (h->prm.vanka_fp16) {
-          invh[l] = h->dalloc((size_t)(lv.Np / lv.npc) * vanka_inv_entries(lv) * 2);
+          invh[l] = h->dalloc((size_t)(lv.Np / lv.npc) * vanka_inv_entries(lv, 2) * 2);
           iscale[l] = (float*)h->dalloc((size_t)(lv.Np / lv.npc) * (lv.k + 1) * sizeof(float));
         } else {
-          inv[l] = (T*)h->dalloc((size_t)(lv.Np / lv.npc) * vanka_inv_entries(lv) * sizeof(T));
+          inv[l] = (T*)h->dalloc((size_t)(lv.Np / lv.npc) * vanka_inv_entries(lv, (int)sizeof(T)) * sizeof(T));
         }
         size_t nc = lv.Np / lv.npc;
         const size_t ec = vanka_elem_cells(lv);                 // element scratch: one chunk

@@ -78,7 +78,7 @@ cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const 
                         unsigned extra_tx = 0);   // extra_tx: failure-test hook (see stmg_test_wait_timeout)
 size_t vanka_spatial_size(const Level& lv);          // m_s = d (r+2)^d + npc
 size_t vanka_patch_size(const Level& lv);            // m_st = (k+1) m_s
-size_t vanka_inv_entries(const Level& lv);           // stored reals of one cell's patch inverse ((k+1) m_s x stride)
+size_t vanka_inv_entries(const Level& lv, int es);   // stored reals of one cell's patch inverse ((k+1) m_s x stride), es-byte entries
 size_t vanka_elem_size(const Level& lv, int which);  // entries per cell of EA (0), EB (1), EM (2)
 bool vanka_supported(const Level& lv, size_t esize);
 

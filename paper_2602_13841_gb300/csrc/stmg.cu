@@ -183,8 +183,10 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
     tot += 5.0 * nst[l] * es;                                            // level vectors
     if (l + 1 < lv.size()) {
       double nl = std::pow(lr + 2.0, d), mv = d * nl, msp = mv + npc;
-      const double st = std::ceil(msp / 8.0) * 8.0;                      // padded column stride
-      const double ent = (lk + 1.0) * msp * st;                          // time-diagonalised inverse
+      const int esz = p->vanka_fp16 ? 2 : (int)es;
+      int sti = (int)msp;                                                // padded column stride
+      while (((long long)msp * sti * esz) % 16 != 0) ++sti;
+      const double ent = (lk + 1.0) * msp * sti;                         // time-diagonalised inverse
       tot += p->vanka_fp16 ? cells * (ent * 2.0 + 4.0 * (lk + 1.0)) : cells * ent * es;  // patch inverses
       // element-matrix scratch: chunks of cell planes, at most ~2^18 cells (three planes at least)
       const double plane = cells / ln, cap = p->build_chunk_cells > 0 ? (double)p->build_chunk_cells : 262144.0;

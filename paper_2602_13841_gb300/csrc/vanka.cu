@@ -198,9 +198,9 @@ static cudaError_t apply_dn(const Level& lv, const Problem& pb, const T* inv, co
   return cudaGetLastError();
 }
 
-size_t vanka_inv_entries(const Level& lv) {
+size_t vanka_inv_entries(const Level& lv, int es) {
   const size_t ms = vanka_spatial_size(lv);
-  return (size_t)(lv.k + 1) * ms * (size_t)inv_stride((int)ms);
+  return (size_t)(lv.k + 1) * ms * (size_t)inv_stride((int)ms, es);
 }
 
 template <typename T>

@@ -31,7 +31,7 @@ struct VankaArgs {
   T* EM;                // [cells][nl][nl]    one scratch; cell c is stored at c - ebase)
   int64_t ebase;
   // Patch inverse of a cell, time-diagonalised: one spatial inverse T_e^{-1} (size m_s = mv +
-  // npc) per eigen-block e, column-major with padded stride inv_stride(m_s); a complex block
+  // npc) per eigen-block e, column-major with stride inv_stride(m_s, element size); a complex block
   // stores (re, im) pairs.  k+1 units of m_s x stride reals per cell, storage in T, or
   T* inv;
   __half* invh;         // the same scaled to [-1, 1] in FP16 with one FP32 factor per block
@@ -41,8 +41,14 @@ struct VankaArgs {
   int64_t wslot;        // ... entries per block slot
 };
 
-// Column stride of a stored patch inverse: m rounded up to 8 entries (16-byte aligned columns).
-__host__ __device__ inline int inv_stride(int m) { return (m + 7) & ~7; }
+// Column stride of a stored patch inverse: the smallest st >= m for which one m x st block of
+// `es`-byte entries is a whole number of 16-byte units, so that every block and every cell's blob
+// starts 16-byte aligned (the bulk copy's requirement) with the least padding (FP32, m = 38: 38).
+__host__ __device__ inline int inv_stride(int m, int es) {
+  int st = m;
+  while (((long long)m * st * es) % 16 != 0) ++st;
+  return st;
+}
 
 // max |x| over the block (all threads receive it)
 template <typename T>
@@ -431,7 +437,7 @@ __device__ bool patch_cell(const VankaArgs<T>& V, const Tab<T>& tb, const TEig<T
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int npc = tb.npc, kp1 = tb.k + 1;
-  const int ms = MV + npc, st = inv_stride(ms);
+  const int ms = MV + npc, st = inv_stride(ms, V.invh ? 2 : (int)sizeof(T));
   const LevelArgs<T>& L = V.L;
   int cc[3] = {0, 0, 0};
   cell_coords<D>(cell, L.n, cc);
@@ -642,7 +648,7 @@ template <> struct InvLd<__half> {
 
 // Dynamic shared memory of k_vanka_apply: [blob | rt (kp1 x mr T) | gb (ms int64) | mbarrier].
 __host__ __device__ inline size_t apply_blob_bytes(int kp1, int ms, size_t si) {
-  return ((size_t)kp1 * ms * inv_stride(ms) * si + 127) & ~(size_t)127;
+  return ((size_t)kp1 * ms * inv_stride(ms, (int)si) * si + 127) & ~(size_t)127;
 }
 __host__ __device__ inline size_t apply_smem_bytes(int kp1, int ms, size_t si, size_t t) {
   const int mr = (ms + 1) & ~1;
@@ -659,7 +665,7 @@ __global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const 
                               TEig<T> te, ColorInfo ci, int* __restrict__ wstat, unsigned extra_tx) {
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
-  const int ms = MV + npc, st = inv_stride(ms), mr = (ms + 1) & ~1;
+  const int ms = MV + npc, st = inv_stride(ms, (int)sizeof(SI)), mr = (ms + 1) & ~1;
   // small patches: several cells per block (slots of tpc threads), so that more cells are in
   // flight than the 32-blocks-per-SM limit would allow with one-warp blocks
   const int tpc = ((ms + 31) / 32) * 32, slot = threadIdx.x / tpc;
@@ -794,7 +800,7 @@ __global__ void k_vanka_apply_global(LevelArgs<T> L, const SI* __restrict__ inv,
                                      int npc, TEig<T> te, ColorInfo ci) {
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
-  const int ms = MV + npc, st = inv_stride(ms), mr = (ms + 1) & ~1;
+  const int ms = MV + npc, st = inv_stride(ms, (int)sizeof(SI)), mr = (ms + 1) & ~1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* rt = reinterpret_cast<T*>(smem_raw);                                              // [kp1 units][mr]
   int64_t* gb = reinterpret_cast<int64_t*>(smem_raw + (((size_t)kp1 * mr * sizeof(T) + 7) & ~(size_t)7));
