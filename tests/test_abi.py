@@ -46,3 +46,15 @@ def test_binding_rejects_missing_library(monkeypatch, tmp_path):
     monkeypatch.setattr(stmg, "LIBPATH", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError):
         stmg.load()
+
+
+def test_footprint_follows_the_hierarchy_option():
+    """stmg_footprint (host arithmetic, no allocation): with DG(k) kept on the coarse levels
+    (keep_time_degree = 1) the levels below the finest carry k + 1 instead of k/2 + 1 time nodes,
+    so the footprint grows; for k = 1 (nothing to coarsen in time) it is unchanged."""
+    from paper_2602_13841_gb300 import stmg
+    build_and_load()
+    fp = lambda **kw: stmg.footprint(stmg.default_params(**dict(dict(dim=2, n_cells_1d=64, r=2), **kw)))
+    assert fp(k=2, keep_time_degree=1) > fp(k=2, keep_time_degree=0)
+    assert fp(k=1, keep_time_degree=1) == fp(k=1, keep_time_degree=0)
+    assert fp(k=2, problem="CAV3D", dim=3, n_cells_1d=8) > 0
