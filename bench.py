@@ -520,7 +520,7 @@ def _peaks():
 
 # DRAM bytes (read + write) per cell of the finest-level Vanka apply, FP32 inverses, Q3/P2/DG(2):
 # ncu capture of one colour launch on the 192^2 mesh of the same recipe, 180.53 MB for 9216
-# cells (profiles/k_vanka_apply_2d_192sq_q3p2_dg2_fp32.md); scaled to a 256^2 launch by its cells.
+# cells; scaled to a 256^2 launch by its cells.
 VANKA_DRAM_BYTES_PER_CELL = 180.529664e6 / 9216
 
 

@@ -160,20 +160,21 @@ stmg_status stmg_smoother_sweep(stmg_handle* h, int level, const void* rhs, void
                                 int zero_start);
 
 /* The same sweep as stmg_smoother_sweep, for callers that must not allocate device memory
- * during the call: code that records work into a CUDA graph by stream capture (an allocation
- * there fails or breaks the capture), real-time loops that forbid allocator calls, or
- * applications whose memory pool is fixed after start-up.  The paper has no counterpart; this
- * is a property of the library, not of the method.
+ * during the call: real-time loops that forbid allocator calls once they run, and applications
+ * that reserve all device memory in a fixed pool at start-up and may not grow it later.  The
+ * paper has no counterpart; this is a property of the library, not of the method.
  * The residual r - J d of each sweep is kept in a fixed 4 MiB device array that every GPU
  * loading this library holds until the process exits; the level's n_st entries in the
  * preconditioner precision must fit in it (at most 524288 doubles or 1048576 floats), else the
  * call returns STMG_ERR_ARG and does nothing.  Nothing is allocated: the handle's patch inverses
  * and level state come from an earlier stmg_smoother_build.  The first call on a device looks up
  * the array's device address with that device current; make that first call before any stream
- * capture.  The array is shared by all calls and keeps the last call's contents (each sweep
- * overwrites it fully before reading it); calls that overlap on the GPU, e.g. from two streams,
- * race on it and must be serialised by the caller.  Arguments and results as in
- * stmg_smoother_sweep. */
+ * capture.  The current device must be the one the handle was created on (else STMG_ERR_ARG).
+ * The array is shared by all calls and keeps the last call's contents (each sweep overwrites it
+ * fully before reading it); calls that overlap on the GPU, e.g. from two streams, race on it and
+ * must be serialised by the caller.  Like stmg_smoother_sweep, the call ends by reading the
+ * device flag of the bounded waits, so it synchronises the handle's stream before it returns
+ * (STMG_ERR_TIMEOUT if a wait ran out).  Arguments and results as in stmg_smoother_sweep. */
 stmg_status stmg_smoother_sweep_noalloc(stmg_handle* h, int level, const void* rhs, void* d, int nsweeps,
                                         int zero_start);
 

@@ -41,6 +41,7 @@ struct CudaFailure : std::runtime_error {
 struct Handle {
   stmg_params prm{};
   cudaStream_t stream = nullptr;
+  int device = 0;                     // the CUDA device that was current at stmg_create
   Problem pb{};
   std::vector<Level> levels;
   std::vector<void*> allocs;

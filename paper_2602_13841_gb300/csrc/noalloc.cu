@@ -57,7 +57,7 @@ static cudaError_t sweep_noalloc(Handle* h, MG<T>& mg, int l, const T* rhs, T* d
     }
     for (int c = 0; c < lv.ncolors; ++c) {
       cudaError_t e = vanka_apply<T>(lv, h->pb, mg.inv[l], mg.invh[l], mg.iscale[l], res, d, h->prm.omega,
-                                     h->prm.omega_p, c, mg.wstat, s);
+                                     h->prm.omega_p, c, mg.wstat, s, h->wait_fault ? 16u : 0u);
       if (e != cudaSuccess) return e;
     }
   }
@@ -83,6 +83,14 @@ extern "C" stmg_status stmg_smoother_sweep_noalloc(stmg_handle* hh, int level, c
     return h->fail(STMG_ERR_ARG, "smoother_sweep_noalloc: level vector of " + std::to_string(need) +
                                      " bytes exceeds the fixed scratch of " + std::to_string(kNoallocScratchBytes) +
                                      " bytes");
+  // the array's address is per device: look it up on the device the handle's stream belongs to
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != h->device) {
+    cudaGetLastError();
+    return h->fail(STMG_ERR_ARG, "smoother_sweep_noalloc: the current CUDA device (" + std::to_string(cur) +
+                                     ") is not the device the handle was created on (" +
+                                     std::to_string(h->device) + ")");
+  }
   void* q = nullptr;
   cudaError_t e = scratch_address(&q);
   if (e != cudaSuccess)

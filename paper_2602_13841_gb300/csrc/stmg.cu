@@ -231,6 +231,7 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
   // omega <= 0: 1.2 / 2^d -- each velocity vertex lies in up to 2^d of the additive patches
   if (!(h->prm.omega > 0)) h->prm.omega = 1.2 / (double)(1 << p->dim);
   h->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { cudaGetLastError(); return STMG_ERR_CUDA; }
   h->pb = Problem{p->nu, p->tau, p->gamma1, p->gamma2, p->bconv, p->problem};
   const int d = p->dim, n = p->n_cells_1d;
   std::vector<double> verts;

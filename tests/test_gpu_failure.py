@@ -48,3 +48,31 @@ def test_vanka_wait_timeout_is_reported_and_the_handle_recovers(r):
     torch.cuda.synchronize()
     assert torch.equal(d, d_ref)
     assert float((d - d0).abs().max()) > 0.0
+
+
+def test_noalloc_sweep_reports_the_wait_timeout_too():
+    """The allocation-free sweep shares the Vanka apply and its bounded wait: with the hook on it
+    must also return STMG_ERR_TIMEOUT, and the handle must recover afterwards."""
+    import torch
+    from paper_2602_13841_gb300 import inputs
+    S = _handle(1)
+    L = S.levels[0]
+    lib = S.lib
+    lib.stmg_smoother_sweep_noalloc.restype = ctypes.c_int
+    lib.stmg_smoother_sweep_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_int, ctypes.c_int]
+    rhs = torch.tensor(inputs.uniform(L["Nst"], 11), dtype=torch.float32, device="cuda")
+    d0 = torch.tensor(inputs.uniform(L["Nst"], 12), dtype=torch.float32, device="cuda")
+    assert lib.stmg_test_wait_timeout(S.h, 1) == 0
+    d = d0.clone()
+    st = lib.stmg_smoother_sweep_noalloc(S.h, 0, ctypes.c_void_p(rhs.data_ptr()), ctypes.c_void_p(d.data_ptr()), 1, 0)
+    assert st == 6, st
+    assert b"bounded wait" in lib.stmg_last_error(S.h)
+    assert lib.stmg_test_wait_timeout(S.h, 0) == 0
+    d = d0.clone()
+    assert lib.stmg_smoother_sweep_noalloc(S.h, 0, ctypes.c_void_p(rhs.data_ptr()), ctypes.c_void_p(d.data_ptr()),
+                                           1, 0) == 0
+    d_ref = d0.clone()
+    S.smoother_sweep(0, rhs, d_ref, 1, zero_start=False)
+    torch.cuda.synchronize()
+    assert torch.equal(d, d_ref)

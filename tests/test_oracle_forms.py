@@ -35,8 +35,9 @@ def perturbed_vertices(d, n, amp, seed):
 
 
 # ----------------------------------------------------------------------------- brute force
-def _brute_force_operator(n, r, nu, V, g1, g2):
-    """Spatial Jacobian [[A, B^T], [B, 0]] of one time node on the Cartesian n x n mesh."""
+def _brute_force_operator(n, r, nu, V, g1, g2, with_mass=False):
+    """Spatial Jacobian [[A, B^T], [B, 0]] of one time node on the Cartesian n x n mesh (and,
+    with_mass, the velocity mass matrix of both components)."""
     gll = {3: [0.0, 0.5, 1.0], 4: [0.0, 0.5 - 5 ** 0.5 / 10, 0.5 + 5 ** 0.5 / 10, 1.0]}[r + 2]
     with warnings.catch_warnings():
         warnings.simplefilter("ignore", DeprecationWarning)
@@ -84,6 +85,7 @@ def _brute_force_operator(n, r, nu, V, g1, g2):
                     px.append((cx + xg[a]) * h); py.append((cy + xg[b]) * h); pw.append(wg[a] * wg[b] * h * h)
     px, py, pw = map(np.array, (px, py, pw))
     Phi, dPhi, Psi = basis_at(px, py)
+    Ms = np.einsum("p,pi,pj->ij", pw, Phi, Phi)
     v = np.stack([Phi @ V[:nn], Phi @ V[nn:]], -1)
     for c in range(2):
         for e in range(2):
@@ -127,6 +129,8 @@ def _brute_force_operator(n, r, nu, V, g1, g2):
                     blk += nrm[e] * np.einsum("p,p,p,pj,pi->ij", pw, 0.5 * (3 - np.sign(y)), v[:, c], Phi, Phi)
                     A[c * nn:(c + 1) * nn, e * nn:(e + 1) * nn] += blk
                 B[:, c * nn:(c + 1) * nn] += nrm[c] * np.einsum("p,pm,pj->mj", pw, Psi, Phi)
+    if with_mass:
+        return A, B, np.kron(np.eye(2), Ms)
     return A, B
 
 
