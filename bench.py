@@ -46,11 +46,12 @@ METRIC = "ST operator apply GDoF/s; Newton-GMRES slab-solve time; serving p50/p9
 WORKLOAD = dict(d=2, n=256, r=2, k=2, amp=0.1, seed=1234, nu=1e-3, tau=0.05, problem="TG2D")
 WORKLOAD_NAME = ("2D unit square 256x256 mapped (amp 0.1h, seed 1234), Q3/P2disc (r=2), DG(2), "
                  "dt=0.05, Re=1000 Taylor-Green; FP32 hp-STMG in FP64 Newton-FGMRES, "
-                 "||R||_M <= max(1e-10 ||R_0||_M, 1e-14)")
-# Absolute floor of the Newton test in the mass-weighted norm.  The Newton guess (the previous
-# slab's end value at every time node) makes ||R_0||_M ~ 1.8e-8 on this workload, so 1e-10
-# relative alone would ask for 1.8e-18, below what the FP64 residual resolves.
-ATOL = 1e-14
+                 "Newton stops at ||R||_M <= 1e-10 ||R_0||_M (relative criterion, no absolute floor)")
+# Absolute floor of the Newton test in the mass-weighted norm: none.  Measured on this workload
+# (first slab, ||R_0||_M = 1.77e-8, Newton capped at m steps, both preconditioner precisions):
+# ||R||_M after 6, 7, 8 steps = 9.1e-18, 6.5e-19, 1.04e-19 (5.9e-12 relative) and still falling, so
+# the FP64 residual resolves the 1e-10 relative target (1.77e-18) with room to spare.
+ATOL = 0.0
 # Smoother of both arms: omega = 1.2 / 2^d (library default), pressure relaxation 1, five pre-
 # and five post-sweeps per level (the lowest time to the Newton tolerance on this workload).
 SMOOTH = dict(nu1=5, nu2=5, omega_p=1.0)

@@ -54,7 +54,16 @@ typedef enum { STMG_FP64 = 0, STMG_FP32 = 1 } stmg_precision;
 /* Analytic data sets of the bundled workloads (f, g, v0).  STMG_CAV3D: the lid-driven cavity of
    Sec. 5.2 on [0,1]^3 -- f = 0, v0 = 0, no-slip walls, and on the lid z = 1 the tangential
    velocity (sin(pi t / 4), 0, 0) (the paper prints the scalar profile; the lid moves along x). */
-typedef enum { STMG_TG2D = 0, STMG_MMS2D = 1, STMG_TG3D = 2, STMG_MMS3D = 3, STMG_CAV3D = 4 } stmg_problem;
+typedef enum { STMG_TG2D = 0, STMG_MMS2D = 1, STMG_TG3D = 2, STMG_MMS3D = 3, STMG_CAV3D = 4,
+               STMG_USER = 5 /* f, g, v0 from caller callbacks (stmg_set_data, stmg_initial_condition);
+                                zero until stmg_set_data is called */ } stmg_problem;
+
+/* A vector field given by the caller (Sec. 2, Problem 2.1: the body force f, the Dirichlet data g
+ * and the initial velocity v0 are data of the problem).  The library calls it on the host with
+ * npts points x (dim x npts doubles, structure of arrays: x[i * npts + p] is coordinate i of point
+ * p) at time t and expects the field in out (dim x npts doubles, same layout; out is zeroed before
+ * the call).  user is the pointer given with the callback.  Values must be finite. */
+typedef void (*stmg_field_fn)(void* user, int64_t npts, const double* x, double t, double* out);
 
 typedef struct {
   int dim;             /* d in {2, 3} */
@@ -88,6 +97,14 @@ typedef struct {
                           ((k, r) -> (k/2, r/2), Sec. 4.2).  1: p-coarsen in space only and keep
                           DG(k) on every level (a variant; the coarse levels cost (k+1)/(k/2+1)
                           times more, the V-cycle contracts faster when k >= 2) */
+  int smoother;        /* 0 (default): the inexact space-time Vanka of Sec. 4.3 (midpoint-surrogate
+                          patch matrices, exact patch inverse).  1: diagonal space-time Vanka, the
+                          cheaper smoother the paper's closing section proposes: the patch's velocity
+                          block keeps only the (k+1) x (k+1) temporal block of each spatial velocity
+                          DoF with itself, the pressure coupling stays whole, and the modified patch
+                          is solved exactly through its (k+1) C(r+d,d) pressure Schur complement
+                          (storage per cell (k+1)^2 m_v + C(r+d,d) m_v + ((k+1) C(r+d,d))^2 reals,
+                          m_v = d (r+2)^d; vanka_fp16 does not apply) */
 } stmg_params;
 
 /* Fill *p with the paper's defaults (Sec. 5, Alg. 1-2) for a d-dimensional problem. */
@@ -132,9 +149,24 @@ stmg_status stmg_apply(stmg_handle* h, int level, int precision, const void* U_s
 stmg_status stmg_residual(stmg_handle* h, double t_start, const double* U, const double* V_prev,
                           double* R);
 
-/* Nodal interpolation of the problem's initial velocity v0 at the velocity nodes (finest
- * level): V0 receives n_v doubles (device). */
-stmg_status stmg_initial_condition(stmg_handle* h, double* V0);
+/* Data of the slab problem given by the caller (Sec. 2, Problem 2.1; Eq. DefFn, DefLn): the body
+ * force f (the term F_n of the residual) and the Dirichlet data g of the Nitsche terms (L_n and
+ * the boundary convection pairing, Eq. bttp), both host callbacks, either may be NULL (zero field).
+ * Switches the handle to problem STMG_USER.  Before each residual of a slab (t_start, t_start +
+ * tau] the library evaluates f at the (r+2)^d Gauss points of every finest-level cell and g at the
+ * (r+2)^(d-1) Gauss points of every boundary face, at the k+1 Radau times of the slab, and keeps
+ * the values on the device (d (k+1) n^d (r+2)^d + 2 d^2 (k+1) n^(d-1) (r+2)^(d-1) doubles,
+ * allocated by the first call; the evaluation is repeated only when t_start or tau change).  The
+ * callbacks run on the calling host thread inside stmg_residual / stmg_slab_solve; user must stay
+ * valid while the handle uses them.  STMG_ERR_NUMERIC from those calls if a callback returns a
+ * non-finite value, STMG_ERR_OOM if the tables do not fit. */
+stmg_status stmg_set_data(stmg_handle* h, stmg_field_fn f, stmg_field_fn g, void* user);
+
+/* Nodal interpolation of the initial velocity at the velocity nodes of the finest level (the
+ * mapped Gauss-Lobatto nodes): V0 receives n_v doubles (device, component-major).  v0 != NULL:
+ * the caller's field, evaluated on the host at t = 0 and copied to V0 (the call returns when the
+ * copy is complete); v0 == NULL: the problem's own initial velocity (zero for STMG_USER). */
+stmg_status stmg_initial_condition(stmg_handle* h, stmg_field_fn v0, void* user, double* V0);
 
 /* Newton initial guess: U (n_st doubles, device) gets V_prev (n_v doubles, device) at every
  * time node and zero pressure. */

@@ -218,6 +218,34 @@ class Vanka:
         return d + self.weights * upd
 
 
+class DiagonalVanka(Vanka):
+    """Diagonal space-time Vanka, the cheaper smoother of the paper's closing section (diagonal
+    Vanka of John 2000, carried to the space-time patch): the velocity block of the surrogate
+    patch matrix keeps only the entries that couple a spatial velocity DoF with itself -- one
+    (k+1) x (k+1) temporal block K^tau M_ii + W A_ii per spatial DoF -- while the pressure
+    coupling W (x) B_K stays whole.  The modified patch is solved exactly (dense LU here; the
+    device solves it through its pressure Schur complement).
+
+    The patch ordering is that of patch_dofs: velocity [time node][component][node], then
+    pressure; spatial velocity DoF of a patch row = its position modulo d * nloc."""
+
+    def __init__(self, level, U, omega, omega_p=None):
+        super().__init__(level, U, omega, omega_p)
+        vstar = midpoint_velocity(level, U)
+        Jt = forms.jacobian(level.space, level.td, U, level.nu, *level.gamma, level.bconv, vstar=vstar,
+                            hscale=level.hscale).tocsr()
+        ms_v = level.d * level.space.nloc
+        nvp = (level.k + 1) * ms_v
+        sid = np.arange(nvp) % ms_v
+        keep = sid[:, None] == sid[None, :]
+        self.patches = []
+        for c in range(level.space.mesh.ncells):
+            idx = patch_dofs(level, c)
+            S = Jt[idx][:, idx].toarray()
+            S[:nvp, :nvp] *= keep
+            self.patches.append((idx, sla.lu_factor(S)))
+
+
 class CoarseSolver:
     """Dense LU of the Jacobian bordered by the mean-zero pressure rows of every time node."""
 
@@ -243,7 +271,7 @@ class Multigrid:
     """hp-STMG V-cycle: z = B^{-1} r on the finest level (Sec. 4.2)."""
 
     def __init__(self, d, n, r, k, vertices, tau, nu, omega=None, nu1=1, nu2=1, omega_p=1.0,
-                 gamma=(10.0, 10.0), bconv=True, max_h=-1, keep_k=False):
+                 gamma=(10.0, 10.0), bconv=True, max_h=-1, keep_k=False, smoother="vanka"):
         # Eq. vanka0 leaves omega open; the additive sum puts each velocity vertex in up to 2^d
         # patches, so the default damping is 1.2 / 2^d (0.3 in 2D, 0.15 in 3D)
         if omega is None:
@@ -257,6 +285,8 @@ class Multigrid:
             self.P.append(P)
             self.I.append(I)
         self.omega, self.omega_p, self.nu1, self.nu2 = omega, omega_p, nu1, nu2
+        # "vanka": the midpoint-surrogate patches of Sec. 4.3; "diagonal": DiagonalVanka
+        self.smoother_cls = {"vanka": Vanka, "diagonal": DiagonalVanka}[smoother]
 
     def level_states(self, U):
         """Velocity state of every level (pressure entries zero) from the fine slab vector."""
@@ -273,7 +303,8 @@ class Multigrid:
         self.states = self.level_states(U)
         self.J = [forms.jacobian(L.space, L.td, S, L.nu, *L.gamma, L.bconv, hscale=L.hscale)
                   for L, S in zip(self.levels, self.states)]
-        self.smoothers = [Vanka(L, S, self.omega, self.omega_p) for L, S in zip(self.levels[:-1], self.states[:-1])]
+        self.smoothers = [self.smoother_cls(L, S, self.omega, self.omega_p)
+                          for L, S in zip(self.levels[:-1], self.states[:-1])]
         self.coarse = CoarseSolver(self.levels[-1], self.J[-1])
 
     def vcycle(self, r, l=0):

@@ -1,8 +1,8 @@
 // Coarsest-level direct solve (Sec. 4.2, "solved directly").  The coarse Jacobian is assembled
 // column by column by a batched matrix-free apply to the identity, bordered with one mean-zero
 // pressure row and column per time node (pure Dirichlet: pressure in L^2_0), inverted once per
-// smoother build by single-block Gauss-Jordan in FP32, and applied with two steps of FP64
-// iterative refinement against the FP64 bordered matrix, so the coarse solution is FP64-accurate.
+// smoother build by Gauss-Jordan elimination with partial pivoting in FP64, and applied in FP64
+// with one step of iterative refinement against the bordered matrix.
 #include "mg.hpp"
 #include "op_launch.cuh"
 #include "vanka.cuh"
@@ -52,24 +52,24 @@ cudaError_t coarse_border(const Level& lv, const Problem& pb, const double* J, d
   return cudaGetLastError();
 }
 
-__global__ void k_to_rowmajor32(const double* __restrict__ A, float* __restrict__ S, int n) {
+__global__ void k_to_rowmajor(const double* __restrict__ A, double* __restrict__ S, int n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
        e += (int64_t)gridDim.x * blockDim.x) {
     int row = (int)(e / n), col = (int)(e % n);
-    S[e] = (float)A[(int64_t)col * n + row];
+    S[e] = A[(int64_t)col * n + row];
   }
 }
 
-__global__ void k_gj_single(float* S, int n, float* col, int* piv, int* status) {
-  bool ok = gauss_jordan<float>(S, n, n, piv, col);
+__global__ void k_gj_single(double* S, int n, double* col, int* piv, int* status) {
+  bool ok = gauss_jordan<double>(S, n, n, piv, col);
   if (!ok && threadIdx.x == 0) *status = 1;
 }
 
-__global__ void k_transpose32(float* S, int n) {
+__global__ void k_transpose(double* S, int n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
        e += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(e / n), j = (int)(e % n);
-    if (i < j) { float t = S[(int64_t)i * n + j]; S[(int64_t)i * n + j] = S[(int64_t)j * n + i]; S[(int64_t)j * n + i] = t; }
+    if (i < j) { double t = S[(int64_t)i * n + j]; S[(int64_t)i * n + j] = S[(int64_t)j * n + i]; S[(int64_t)j * n + i] = t; }
   }
 }
 
@@ -78,52 +78,52 @@ __global__ void k_transpose32(float* S, int n) {
 // scales it and moves column p into `col`; k_gj_elim (all SMs) updates the other rows; after the
 // last step k_gj_unswap (one block) undoes the column exchanges.  A zero pivot sets *status and
 // turns the remaining steps into no-ops.
-__global__ void k_gj_pivot(float* S, int n, int p, float* col, int* piv, int* status) {
+__global__ void k_gj_pivot(double* S, int n, int p, double* col, int* piv, int* status) {
   __shared__ int s_r;
-  __shared__ float s_best[32];
+  __shared__ double s_best[32];
   __shared__ int s_idx[32];
   if (*status) return;
   const int tid = threadIdx.x, nt = blockDim.x;
-  float best = -1.f; int bi = p;
+  double best = -1.0; int bi = p;
   for (int i = p + tid; i < n; i += nt) {
-    const float a = fabsf(S[(int64_t)i * n + p]);
+    const double a = fabs(S[(int64_t)i * n + p]);
     if (a > best || (a == best && i < bi)) { best = a; bi = i; }
   }
   for (int off = 16; off > 0; off >>= 1) {
-    const float ob = __shfl_down_sync(0xffffffffu, best, off);
+    const double ob = __shfl_down_sync(0xffffffffu, best, off);
     const int oi = __shfl_down_sync(0xffffffffu, bi, off);
     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
   }
   if ((tid & 31) == 0) { s_best[tid >> 5] = best; s_idx[tid >> 5] = bi; }
   __syncthreads();
   if (tid < 32) {
-    best = tid < (nt >> 5) ? s_best[tid] : -1.f;
+    best = tid < (nt >> 5) ? s_best[tid] : -1.0;
     bi = tid < (nt >> 5) ? s_idx[tid] : p;
     for (int off = 16; off > 0; off >>= 1) {
-      const float ob = __shfl_down_sync(0xffffffffu, best, off);
+      const double ob = __shfl_down_sync(0xffffffffu, best, off);
       const int oi = __shfl_down_sync(0xffffffffu, bi, off);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
-    if (tid == 0) { s_r = bi; piv[p] = bi; if (!(best > 0.f)) *status = 1; }
+    if (tid == 0) { s_r = bi; piv[p] = bi; if (!(best > 0.0)) *status = 1; }
   }
   __syncthreads();
   if (*status) return;
   const int r = s_r;
   if (r != p)
     for (int j = tid; j < n; j += nt) {
-      const float t = S[(int64_t)p * n + j]; S[(int64_t)p * n + j] = S[(int64_t)r * n + j]; S[(int64_t)r * n + j] = t;
+      const double t = S[(int64_t)p * n + j]; S[(int64_t)p * n + j] = S[(int64_t)r * n + j]; S[(int64_t)r * n + j] = t;
     }
   __syncthreads();
-  const float pinv = 1.f / S[(int64_t)p * n + p];
+  const double pinv = 1.0 / S[(int64_t)p * n + p];
   __syncthreads();
   for (int j = tid; j < n; j += nt) S[(int64_t)p * n + j] = (j == p) ? pinv : S[(int64_t)p * n + j] * pinv;
   for (int i = tid; i < n; i += nt) {
-    col[i] = (i == p) ? 0.f : S[(int64_t)i * n + p];
-    if (i != p) S[(int64_t)i * n + p] = 0.f;
+    col[i] = (i == p) ? 0.0 : S[(int64_t)i * n + p];
+    if (i != p) S[(int64_t)i * n + p] = 0.0;
   }
 }
 
-__global__ void k_gj_elim(float* S, int n, int p, const float* __restrict__ col, const int* status) {
+__global__ void k_gj_elim(double* S, int n, int p, const double* __restrict__ col, const int* status) {
   if (*status) return;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -132,21 +132,21 @@ __global__ void k_gj_elim(float* S, int n, int p, const float* __restrict__ col,
   }
 }
 
-__global__ void k_gj_unswap(float* S, int n, const int* __restrict__ piv, const int* status) {
+__global__ void k_gj_unswap(double* S, int n, const int* __restrict__ piv, const int* status) {
   if (*status) return;
   for (int p = n - 1; p >= 0; --p) {
     const int r = piv[p];
     if (r != p)
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const float t = S[(int64_t)i * n + p]; S[(int64_t)i * n + p] = S[(int64_t)i * n + r]; S[(int64_t)i * n + r] = t;
+        const double t = S[(int64_t)i * n + p]; S[(int64_t)i * n + p] = S[(int64_t)i * n + r]; S[(int64_t)i * n + r] = t;
       }
     __syncthreads();
   }
 }
 
-cudaError_t coarse_invert(const double* A, float* Ainv, float* col, int* piv, int Nb, int* status,
+cudaError_t coarse_invert(const double* A, double* Ainv, double* col, int* piv, int Nb, int* status,
                           cudaStream_t s) {
-  k_to_rowmajor32<<<152 * 4, 256, 0, s>>>(A, Ainv, Nb);
+  k_to_rowmajor<<<152 * 4, 256, 0, s>>>(A, Ainv, Nb);
   note_launch();
   if (Nb <= 512) {
     k_gj_single<<<1, 1024, 0, s>>>(Ainv, Nb, col, piv, status);
@@ -160,7 +160,7 @@ cudaError_t coarse_invert(const double* A, float* Ainv, float* col, int* piv, in
     k_gj_unswap<<<1, 1024, 0, s>>>(Ainv, Nb, piv, status);
     note_launch(2 * Nb + 1);
   }
-  k_transpose32<<<152 * 4, 256, 0, s>>>(Ainv, Nb);    // row-major inverse -> column-major
+  k_transpose<<<152 * 4, 256, 0, s>>>(Ainv, Nb);      // row-major inverse -> column-major
   note_launch();
   return cudaGetLastError();
 }
@@ -180,10 +180,5 @@ cudaError_t gemv_cm(const double* A, int n, const double* x, double* y, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t gemv_cm(const float* A, int n, const double* x, double* y, cudaStream_t s) {
-  k_gemv_cm<float><<<(n + 127) / 128, 128, 0, s>>>(A, n, x, y);
-  note_launch();
-  return cudaGetLastError();
-}
 
 }  // namespace stmg

@@ -112,7 +112,25 @@ struct LevelArgs {
   T hscale;
   int bconv, problem;
   T t0, tau;
+  // STMG_USER data of the slab (finest level, residual only), time node a = 0..k:
+  //   ftab[((a ncells + cell) D + c) Q + q]: f_c at Gauss point q (lexicographic, x fastest) of cell
+  //   gtab[((((a D + axis) 2 + side) nf + f) D + c) NF + p]: g_c at face point p of the boundary
+  //     face (axis, side) of the boundary cell whose other coordinates, lower axis fastest, give f
+  //     (nf = n^(D-1)); face points lexicographic over the other axes, lower axis fastest
+  const double* ftab;
+  const double* gtab;
 };
+
+constexpr int kProblemUser = 5;   // STMG_USER
+
+// Index of the boundary face (axis, side) of cell cc among the n^(D-1) faces of that side.
+template <int D>
+__device__ inline int64_t face_index(const int* cc, int axis, int n) {
+  int64_t f = 0, s = 1;
+  for (int l = 0; l < D; ++l)
+    if (l != axis) { f += cc[l] * s; s *= n; }
+  return f;
+}
 
 // Cells of one colour: coordinates of parity `color` (bit l = parity along axis l).
 struct ColorInfo {

@@ -53,6 +53,16 @@ struct Handle {
   double *Vb = nullptr, *Zb = nullptr, *w = nullptr, *R = nullptr, *dX = nullptr, *Xt = nullptr;
   double *Mv = nullptr, *Jv = nullptr, *pw = nullptr, *scratch = nullptr, *hdev = nullptr;
   int* flag = nullptr;
+  // STMG_USER data: host callbacks, their evaluation points on the finest level (SoA), device
+  // tables of f and g for the slab starting at user_t0 (see LevelArgs::ftab / gtab)
+  stmg_field_fn user_f = nullptr, user_g = nullptr;
+  void* user_ctx = nullptr;
+  std::vector<double> user_fx, user_gx;
+  double* ftab = nullptr;
+  double* gtab = nullptr;
+  double user_t0 = 0.0;
+  bool user_valid = false;
+  std::vector<double> verts0;         // host copy of the finest level's vertices
   bool solver_ready = false;
   bool timing = false;
   bool wait_fault = false;           // failure-test hook: Vanka applies wait for bytes never sent

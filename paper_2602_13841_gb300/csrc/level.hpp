@@ -23,6 +23,7 @@ struct Level {
   int ncolors = 0;
   double hscale = 0;                  // Nitsche length factor (see LevelArgs)
   int64_t chunk_cells = 262144;       // cells per chunk of the smoother build's element scratch
+  int smoother = 0;                   // 0: surrogate patches (Sec. 4.3); 1: diagonal space-time Vanka
   double* geo64 = nullptr;            // 2D: geometry table of the Jacobian apply (see OpArgs::geo)
   float* geo32 = nullptr;
 };
@@ -30,6 +31,11 @@ struct Level {
 struct Problem {
   double nu, tau, gamma1, gamma2;
   int bconv, problem;
+  // STMG_USER: f at the volume Gauss points and g at the boundary-face Gauss points of the
+  // finest level for the current slab (device tables filled from the host callbacks; see
+  // LevelArgs::ftab / gtab for the layout)
+  const double* ftab = nullptr;
+  const double* gtab = nullptr;
 };
 
 template <typename T>
@@ -44,6 +50,12 @@ template <typename T>
 cudaError_t launch_operator(const Level& lv, const Problem& pb, int mode, double t0, const T* x,
                             const T* state, const T* vprev, T* y, cudaStream_t stream,
                             int batch = 1, int64_t xs = 0, int64_t ys = 0);
+
+// y = rhs - J(state) x on a level (rhs null: y = J(state) x), the residual of a multigrid sweep;
+// one launch where the tiled 2D kernel applies, else the operator followed by a vector update.
+template <typename T>
+cudaError_t launch_level_residual(const Level& lv, const Problem& pb, const T* rhs, const T* x, const T* state, T* y,
+                                  cudaStream_t stream);
 
 cudaError_t launch_initial_condition(const Level& lv, const Problem& pb, double* V0, cudaStream_t s);
 

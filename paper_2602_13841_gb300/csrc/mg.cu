@@ -29,7 +29,7 @@ cudaError_t MG<T>::allocate(Handle* hh) {
       if (l < nl - 1) {
         if (!vanka_supported(lv, sizeof(T))) { smoothable = false; continue; }
         size_t m = vanka_patch_size(lv);
-        if (h->prm.vanka_fp16) {
+        if (h->prm.vanka_fp16 && lv.smoother == 0) {
           invh[l] = h->dalloc((size_t)(lv.Np / lv.npc) * vanka_inv_entries(lv, 2) * 2);
           iscale[l] = (float*)h->dalloc((size_t)(lv.Np / lv.npc) * (lv.k + 1) * sizeof(float));
         } else {
@@ -65,8 +65,8 @@ cudaError_t MG<T>::allocate(Handle* hh) {
     cx = (double*)h->dalloc((size_t)Nb * sizeof(double));
     cr = (double*)h->dalloc((size_t)Nb * sizeof(double));
     cw = (double*)h->dalloc((size_t)Nb * sizeof(double));
-    Ainv = (float*)h->dalloc((size_t)Nb * Nb * sizeof(float));
-    gj_col = (float*)h->dalloc((size_t)Nb * sizeof(float));
+    Ainv = (double*)h->dalloc((size_t)Nb * Nb * sizeof(double));
+    gj_col = (double*)h->dalloc((size_t)Nb * sizeof(double));
     gj_piv = (int*)h->dalloc((size_t)Nb * sizeof(int));
   } catch (const std::bad_alloc&) {
     return cudaErrorMemoryAllocation;
@@ -132,7 +132,7 @@ cudaError_t MG<T>::coarse_solve(const T* rhs, T* d) {
   CKE(cudaMemsetAsync(cb, 0, Nb * sizeof(double), s));
   CKE((vcopy<T, double>(Nc, rhs, cb, s)));
   CKE(gemv_cm(Ainv, Nb, cb, cx, s));
-  for (int it = 0; it < 3; ++it) {          // FP64 iterative refinement
+  for (int it = 0; it < 1; ++it) {          // one step of iterative refinement
     CKE(gemv_cm(A64, Nb, cx, cw, s));
     CKE(cudaMemcpyAsync(cr, cb, Nb * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CKE(vaxpby<double>(Nb, -1.0, cw, 1.0, cr, s));
@@ -155,9 +155,8 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
     } else {
       // q = rhs - J d
       h->kbegin(KC_APPLYP);
-      CKE(launch_operator<T>(lv, h->pb, OP_JAC, 0.0, d, U[l], nullptr, q[l], s));
+      CKE(launch_level_residual<T>(lv, h->pb, rhs, d, U[l], q[l], s));
       h->kend(KC_APPLYP);
-      CKE(vaxpby<T>(lv.Nst, (T)1, rhs, (T)-1, q[l], s));
       res = q[l];
     }
     // one timer span over the colour launches of the sweep (they run back to back);
@@ -165,7 +164,8 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
     // per cell: (k+1) m_s^2 stored reals (one spatial inverse per real time eigenvalue, a complex
     // one per conjugate pair), residual gather and d update on the (k+1) m_s patch DoFs
     const double ms = (double)vanka_spatial_size(lv), m = (double)vanka_patch_size(lv);
-    const double ib = (lv.k + 1) * ms * ms * (invh[l] ? 2.0 : (double)sizeof(T)) + (invh[l] ? 4.0 * (lv.k + 1) : 0.0);
+    const double ib = lv.smoother == 1 ? (double)vanka_inv_entries(lv, (int)sizeof(T)) * sizeof(T)
+                      : (lv.k + 1) * ms * ms * (invh[l] ? 2.0 : (double)sizeof(T)) + (invh[l] ? 4.0 * (lv.k + 1) : 0.0);
     int64_t cells = 0;
     h->kbegin(KC_VANKA_APPLY);
     if (l == 0) h->kbegin(KC_VANKA_APPLY0);
@@ -190,9 +190,8 @@ cudaError_t MG<T>::vcycle_level(int l, const T* rhs, T* d) {
   else CKE(cudaMemsetAsync(d, 0, lv.Nst * sizeof(T), s));
   // t = rhs - J d ; r_{l+1} = P^T t
   h->kbegin(KC_APPLYP);
-  CKE(launch_operator<T>(lv, h->pb, OP_JAC, 0.0, d, U[l], nullptr, t[l], s));
+  CKE(launch_level_residual<T>(lv, h->pb, rhs, d, U[l], t[l], s));
   h->kend(KC_APPLYP);
-  CKE(vaxpby<T>(lv.Nst, (T)1, rhs, (T)-1, t[l], s));
   CKE(tr[l].template restrict_<T>(t[l], r[l + 1], s));
   CKE(vcycle_level(l + 1, r[l + 1], z[l + 1]));
   CKE(tr[l].template prolong<T>(z[l + 1], t[l], s));

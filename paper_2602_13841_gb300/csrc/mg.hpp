@@ -30,12 +30,12 @@ struct MG {
   int* status = nullptr;             // device flag: zero pivot in a patch
   int* wstat = nullptr;              // device flag: a bounded wait in the Vanka apply ran out
   cudaError_t check_wait();          // reads and clears wstat (synchronises the stream)
-  // coarsest level: bordered Jacobian (FP64), its FP32 inverse, FP64 refinement buffers
+  // coarsest level: bordered Jacobian (FP64), its FP64 inverse, refinement buffers
   int Nc = 0, Nb = 0;
   double *A64 = nullptr, *Ucs = nullptr, *cb = nullptr, *cx = nullptr, *cr = nullptr, *cw = nullptr;
   double* ident = nullptr;
-  float* Ainv = nullptr;
-  float* gj_col = nullptr;
+  double* Ainv = nullptr;
+  double* gj_col = nullptr;
   int* gj_piv = nullptr;
   bool built = false;
   bool smoothable = true;            // every smoothed level's element matrices fit on-chip memory
@@ -85,9 +85,8 @@ bool vanka_supported(const Level& lv, size_t esize);
 // Coarse solver helpers (coarse.cu)
 cudaError_t coarse_border(const Level& lv, const Problem& pb, const double* J, double* A, int N, int Nb,
                           cudaStream_t s);
-cudaError_t coarse_invert(const double* A, float* Ainv, float* col, int* piv, int Nb, int* status,
+cudaError_t coarse_invert(const double* A, double* Ainv, double* col, int* piv, int Nb, int* status,
                           cudaStream_t s);
 cudaError_t gemv_cm(const double* A, int n, const double* x, double* y, cudaStream_t s);
-cudaError_t gemv_cm(const float* A, int n, const double* x, double* y, cudaStream_t s);
 
 }  // namespace stmg

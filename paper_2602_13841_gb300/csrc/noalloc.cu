@@ -48,10 +48,8 @@ static cudaError_t sweep_noalloc(Handle* h, MG<T>& mg, int l, const T* rhs, T* d
       cudaError_t e = cudaMemsetAsync(d, 0, lv.Nst * sizeof(T), s);
       if (e != cudaSuccess) return e;
     } else {
-      // q = rhs - J d (launch_operator zeroes q before accumulating into it)
-      cudaError_t e = launch_operator<T>(lv, h->pb, OP_JAC, 0.0, d, mg.U[l], nullptr, q, s);
-      if (e != cudaSuccess) return e;
-      e = vaxpby<T>(lv.Nst, (T)1, rhs, (T)-1, q, s);
+      // q = rhs - J d, by the same launches as the regular sweep
+      cudaError_t e = launch_level_residual<T>(lv, h->pb, rhs, d, mg.U[l], q, s);
       if (e != cudaSuccess) return e;
       res = q;
     }

@@ -2,6 +2,7 @@
 // nodal interpolation of the initial velocity.
 #include <type_traits>
 #include "op_launch.cuh"
+#include "vec.cuh"
 
 namespace stmg {
 
@@ -12,6 +13,16 @@ cudaError_t launch_operator<double>(const Level& lv, const Problem& pb, int mode
   if (mode == OP_RES) return launch_any<double, MR>(lv, pb, t0, x, state, vprev, y, s, batch, xs, ys);
   if (mode == OP_MASS) return launch_any<double, MM>(lv, pb, t0, x, state, vprev, y, s, batch, xs, ys);
   return launch_any<double, MJ>(lv, pb, t0, x, state, vprev, y, s, batch, xs, ys);
+}
+
+template <>
+cudaError_t launch_level_residual<double>(const Level& lv, const Problem& pb, const double* rhs, const double* x,
+                                          const double* state, double* y, cudaStream_t s) {
+  cudaError_t e = launch_jac_tiled<double>(lv, pb, x, state, rhs, y, s);
+  if (e != cudaErrorNotSupported) return e;
+  e = launch_any<double, MJ>(lv, pb, 0.0, x, state, nullptr, y, s, 1, 0, 0);
+  if (e == cudaSuccess && rhs) e = vaxpby<double>(lv.Nst, 1.0, rhs, -1.0, y, s);
+  return e;
 }
 
 // v_{0,h}: v0 evaluated at the mapped Gauss-Lobatto nodes (one thread per global node).

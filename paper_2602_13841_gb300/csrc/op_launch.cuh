@@ -4,7 +4,10 @@
 #include "level.hpp"
 #include "operator.cuh"
 #include "operator2d.cuh"
+#include "operator2d_tile.cuh"
 #include "counters.hpp"
+#include <cstdlib>
+#include <cstring>
 
 namespace stmg {
 
@@ -18,6 +21,7 @@ LevelArgs<T> level_args(const Level& lv, const Problem& pb, double t0) {
   a.hscale = (T)lv.hscale;
   a.bconv = pb.bconv; a.problem = pb.problem;
   a.t0 = (T)t0; a.tau = (T)pb.tau;
+  a.ftab = pb.ftab; a.gtab = pb.gtab;
   return a;
 }
 
@@ -87,6 +91,46 @@ static cudaError_t launch_dn(const Level& lv, const Problem& pb, double t0, cons
     }
   }
   return cudaGetLastError();
+}
+
+// Process-wide choice of the 2D Jacobian-apply kernel: the tiled single-launch kernel where it
+// applies (default), or the colour-split warp kernel when the environment variable STMG_APPLY2D
+// is "colour" (kept for comparisons; read once).
+inline bool apply2d_tiled() {
+  static const bool on = [] {
+    const char* v = std::getenv("STMG_APPLY2D");
+    return !(v && std::strcmp(v, "colour") == 0);
+  }();
+  return on;
+}
+
+template <typename T, int N>
+static cudaError_t jac_tiled_n(const Level& lv, const Problem& pb, const T* x, const T* state, const T* rhs, T* y,
+                               cudaStream_t s) {
+  OpArgs<T> A{level_args<T>(lv, pb, 0.0), x, state, nullptr, y, 0, 0, nullptr};
+  const Tab<T> tb = make_tab<T>(lv.tabs, pb.tau);
+  cudaError_t e = cudaErrorNotSupported;
+  if (lv.k == 0) e = launch_apply2d_tile<T, N, 1>(A, tb, rhs, lv.n, s);
+  else if (lv.k == 1) e = launch_apply2d_tile<T, N, 2>(A, tb, rhs, lv.n, s);
+  else if (lv.k == 2) e = launch_apply2d_tile<T, N, 3>(A, tb, rhs, lv.n, s);
+  if (e == cudaSuccess) note_launch();
+  return e;
+}
+
+// y = J(state) x, or y = rhs - J(state) x when rhs is not null, by the tiled 2D kernel (one
+// launch, y written without a zero fill).  cudaErrorNotSupported where it does not apply (3D,
+// Q4/P3, FP64, or the colour kernels chosen).
+template <typename T>
+cudaError_t launch_jac_tiled(const Level& lv, const Problem& pb, const T* x, const T* state, const T* rhs, T* y,
+                             cudaStream_t s) {
+  if constexpr (!std::is_same<T, float>::value) {
+    return cudaErrorNotSupported;
+  } else {
+    if (lv.d != 2 || !apply2d_tiled()) return cudaErrorNotSupported;
+    if (lv.r == 1) return jac_tiled_n<T, 3>(lv, pb, x, state, rhs, y, s);
+    if (lv.r == 2) return jac_tiled_n<T, 4>(lv, pb, x, state, rhs, y, s);
+    return cudaErrorNotSupported;
+  }
 }
 
 template <typename T, int MODE>

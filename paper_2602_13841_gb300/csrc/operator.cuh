@@ -247,7 +247,12 @@ __global__ void k_volume(OpArgs<T> A, Tab<T> tb_p, ColorInfo ci, int cpb) {
         double xd[3], fd[3];
         for (int l = 0; l < D; ++l) xd[l] = (double)xq[l];
         const double ta = (double)L.t0 + 0.5 * (double)L.tau * ((double)tb.that[a] + 1.0);  // t_n^a
-        problem_f<D>(L.problem, xd, ta, (double)L.nu, fd);
+        if (L.problem == kProblemUser) {
+          const int64_t ncells = (int64_t)ipow(L.n, D);
+          for (int c = 0; c < D; ++c) fd[c] = L.ftab[(((int64_t)a * ncells + cell) * D + c) * Q + t];
+        } else {
+          problem_f<D>(L.problem, xd, ta, (double)L.nu, fd);
+        }
         for (int c = 0; c < D; ++c) fq[c] = (T)fd[c];
       }
       for (int c = 0; c < D; ++c) {
@@ -475,7 +480,13 @@ __global__ void k_faces(OpArgs<T> A, Tab<T> tb_p, const int* __restrict__ bcells
             double xd[3], gv[3];
             for (int l = 0; l < D; ++l) xd[l] = (double)xf[l];
             const double ta = (double)L.t0 + 0.5 * (double)L.tau * ((double)tb.that[a] + 1.0);
-            problem_g<D>(L.problem, xd, ta, (double)L.nu, gv);
+            if (L.problem == kProblemUser) {
+              const int64_t nf = (int64_t)ipow(L.n, D - 1), f = face_index<D>(cc, axis, L.n);
+              for (int c = 0; c < D; ++c)
+                gv[c] = L.gtab[(((((int64_t)a * D + axis) * 2 + side) * nf + f) * D + c) * NF + t];
+            } else {
+              problem_g<D>(L.problem, xd, ta, (double)L.nu, gv);
+            }
             for (int c = 0; c < D; ++c) { gd[c] = (T)gv[c]; e[c] = v[c] - gd[c]; }
           } else {
             for (int c = 0; c < D; ++c) e[c] = dv[c];

@@ -141,7 +141,17 @@ __device__ __forceinline__ void face2d(const OpArgs<T>& A, const Tab<T>& tb, int
   if (RES) {
     double xd[3] = {(double)xf[0], (double)xf[1], 0.0}, gv[3];
     const double ta = (double)L.t0 + 0.5 * (double)L.tau * ((double)tb.that[a] + 1.0);
-    problem_g<2>(L.problem, xd, ta, (double)L.nu, gv);
+    if (L.problem == kProblemUser) {
+      if (has) {
+        const int64_t gb = ((((int64_t)a * 2 + axis) * 2 + side) * L.n + cc[1 - axis]) * 2 * N + tt;
+        gv[0] = L.gtab[gb];
+        gv[1] = L.gtab[gb + N];
+      } else {
+        gv[0] = gv[1] = 0.0;
+      }
+    } else {
+      problem_g<2>(L.problem, xd, ta, (double)L.nu, gv);
+    }
     gd[0] = (T)gv[0]; gd[1] = (T)gv[1];
     ev[0] = fs[0] - gd[0]; ev[1] = fs[1] - gd[1];
   } else {
@@ -337,7 +347,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_volume2d(OpArgs
   if (RES && on) {
     double xd[3] = {(double)xq[0], (double)xq[1], 0.0}, fd[3];
     const double ta = (double)L.t0 + 0.5 * (double)L.tau * ((double)tb.that[a] + 1.0);
-    problem_f<2>(L.problem, xd, ta, (double)L.nu, fd);
+    if (L.problem == kProblemUser) {
+      const int64_t fb = (((int64_t)a * L.n * L.n + cell) * 2) * Q + t;
+      fd[0] = L.ftab[fb];
+      fd[1] = L.ftab[fb + Q];
+    } else {
+      problem_f<2>(L.problem, xd, ta, (double)L.nu, fd);
+    }
     fq[0] = (T)fd[0]; fq[1] = (T)fd[1];
   }
   T z[2];

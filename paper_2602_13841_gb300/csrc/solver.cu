@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "handle.hpp"
+#include "userdata.hpp"
 #include "vec.cuh"
 #include "counters.hpp"
 
@@ -271,6 +272,11 @@ static stmg_status newton(Handle* h, MG<T>& mg, double t0, const double* Vprev, 
   const stmg_params& P = h->prm;
   const double eps = 1e-30;
 #define CKS(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return h->fail(e_ == cudaErrorUnknown ? STMG_ERR_NUMERIC : e_ == cudaErrorNotSupported ? STMG_ERR_UNSUPPORTED : STMG_ERR_CUDA, std::string("slab_solve: ") + #x + ": " + cudaGetErrorString(e_)); } while (0)
+  {
+    cudaError_t eu = refresh_user_data(h, t0);
+    if (eu == cudaErrorInvalidValue) return h->fail(STMG_ERR_NUMERIC, "slab_solve: a data callback returned a non-finite value");
+    CKS(eu);
+  }
   CKS(launch_operator<double>(L, h->pb, OP_RES, t0, X, nullptr, Vprev, h->R, s));
   double nr = 0;
   CKS(mnorm(h, h->R, &nr));

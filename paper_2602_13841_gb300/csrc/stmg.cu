@@ -15,6 +15,7 @@
 #include "../../include/stmg.h"
 #include "counters.hpp"
 #include "handle.hpp"
+#include "userdata.hpp"
 
 using namespace stmg;
 
@@ -187,31 +188,38 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
       int sti = (int)msp;                                                // padded column stride
       while (((long long)msp * sti * esz) % 16 != 0) ++sti;
       const double ent = (lk + 1.0) * msp * sti;                         // time-diagonalised inverse
-      tot += p->vanka_fp16 ? cells * (ent * 2.0 + 4.0 * (lk + 1.0)) : cells * ent * es;  // patch inverses
+      if (p->smoother == 1)                                              // diagonal blobs
+        tot += cells * es * (mv * (lk + 1.0) * (lk + 1.0) + npc * mv + (lk + 1.0) * npc * (lk + 1.0) * npc);
+      else
+        tot += p->vanka_fp16 ? cells * (ent * 2.0 + 4.0 * (lk + 1.0)) : cells * ent * es;  // patch inverses
       // element-matrix scratch: chunks of cell planes, at most ~2^18 cells (three planes at least)
       const double plane = cells / ln, cap = p->build_chunk_cells > 0 ? (double)p->build_chunk_cells : 262144.0;
       const double ec = cells <= cap ? cells : std::min(cells, std::max(3.0, std::floor(cap / plane)) * plane);
       ea = std::max(ea, ec * mv * mv); eb = std::max(eb, ec * npc * mv); em = std::max(em, ec * nl * nl);
       // patches beyond shared memory are factorised in a global workspace of 304 block slots
       const double pslot = 2.0 * msp * msp + mv * mv + nl * nl;
-      if (es * (pslot + 2.0 * msp) + 4.0 * msp + 16.0 > 227.0 * 1024.0) wk = std::max(wk, 304.0 * pslot * es);
+      if (p->smoother != 1 && es * (pslot + 2.0 * msp) + 4.0 * msp + 16.0 > 227.0 * 1024.0)
+        wk = std::max(wk, 304.0 * pslot * es);
       nvmax = std::max(nvmax, Nv);
       tot += 3.0 * std::max((lk + 1.0) * Nv, (lk + 1.0) * Np) * es;      // transfer scratch
     }
   }
   tot += (ea + eb + em + nvmax) * es + wk;
   const double Nc = nst.back(), Nb = Nc + lv.back()[2] + 1;
-  tot += Nb * Nb * 12.0 + Nc * Nc * 8.0;                                 // coarse factors
+  tot += Nb * Nb * 16.0 + Nc * Nc * 8.0;                                 // coarse factors
   tot += (2.0 * p->gmres_restart + 1.0 + 9.0) * nst[0] * 8.0;           // Krylov basis, Newton vectors
   *bytes = (uint64_t)tot;
   return STMG_OK;
 }
 
 stmg_status stmg_set_physics(stmg_handle* hh, double nu, double tau, int problem) {
-  if (!hh || !(nu > 0) || !(tau > 0) || problem < STMG_TG2D || problem > STMG_CAV3D) return STMG_ERR_ARG;
+  if (!hh || !(nu > 0) || !(tau > 0) || problem < STMG_TG2D || problem > STMG_USER) return STMG_ERR_ARG;
   Handle* h = reinterpret_cast<Handle*>(hh);
   h->prm.nu = nu; h->prm.tau = tau; h->prm.problem = problem;
   h->pb.nu = nu; h->pb.tau = tau; h->pb.problem = problem;
+  h->pb.ftab = problem == STMG_USER ? h->ftab : nullptr;
+  h->pb.gtab = problem == STMG_USER ? h->gtab : nullptr;
+  h->user_valid = false;                 // tau enters the Radau times of the data tables
   // the captured V-cycle bakes the physics into its kernel parameters
   if (h->mg32) h->mg32->drop_graph();
   if (h->mg64) h->mg64->drop_graph();
@@ -224,7 +232,7 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
   *out = nullptr;
   if (p->dim < 2 || p->dim > 3 || p->r < 1 || p->r > 3 || p->k < 0 || p->k > 2 ||
       p->n_cells_1d < 1 || p->n_cells_1d > 4096 || !(p->tau > 0) || !(p->nu > 0) ||
-      p->problem < STMG_TG2D || p->problem > STMG_CAV3D)
+      p->problem < STMG_TG2D || p->problem > STMG_USER || p->smoother < 0 || p->smoother > 1)
     return STMG_ERR_ARG;
   auto h = std::make_unique<Handle>();
   h->prm = *p;
@@ -247,6 +255,7 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
       for (int l = 0; l < d; ++l) { verts[i * d + l] = (double)(rem % (n + 1)) / n; rem /= (n + 1); }
     }
   }
+  h->verts0 = verts;
   // hierarchy: p-coarsening first (taller of the r / k hierarchies alone until the heights
   // match, then both), then h-coarsening of the space mesh (Sec. 4.2, "cycle and coarsening order")
   try {
@@ -255,6 +264,7 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
     const double p0 = p->r + 1;
     for (auto& rk : pk) {
       Level lv; lv.d = d; lv.n = n; lv.r = rk.first; lv.k = rk.second;
+      lv.smoother = p->smoother == 1 ? 1 : 0;
       if (p->build_chunk_cells > 0) lv.chunk_cells = p->build_chunk_cells;
       lv.hscale = 1.0 / (p0 * (p0 + 1.0));
       build_level(h.get(), lv, verts);
@@ -266,6 +276,7 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
       cv = coarsen_vertices(cv, d, nn);
       nn /= 2; ++hl;
       Level lv; lv.d = d; lv.n = nn; lv.r = r; lv.k = k;
+      lv.smoother = p->smoother == 1 ? 1 : 0;
       if (p->build_chunk_cells > 0) lv.chunk_cells = p->build_chunk_cells;
       lv.hscale = ((double)nn / n) / (p0 * (p0 + 1.0));
       build_level(h.get(), lv, cv);
@@ -358,15 +369,63 @@ stmg_status stmg_residual(stmg_handle* hh, double t_start, const double* U, cons
   if (!hh) return STMG_ERR_ARG;
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!U || !V_prev || !R || R == U) return h->fail(STMG_ERR_ARG, "stmg_residual: bad pointer");
-  cudaError_t e = launch_operator<double>(h->levels[0], h->pb, OP_RES, t_start, U, nullptr, V_prev, R, h->stream);
+  if (h->pb.problem == STMG_USER && !h->ftab)
+    return h->fail(STMG_ERR_ARG, "stmg_residual: problem STMG_USER needs stmg_set_data first");
+  cudaError_t e = refresh_user_data(h, t_start);
+  if (e == cudaErrorInvalidValue) return h->fail(STMG_ERR_NUMERIC, "stmg_residual: a data callback returned a non-finite value");
+  if (e == cudaSuccess) e = launch_operator<double>(h->levels[0], h->pb, OP_RES, t_start, U, nullptr, V_prev, R, h->stream);
   if (e != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string("stmg_residual: ") + cudaGetErrorString(e));
   return STMG_OK;
 }
 
-stmg_status stmg_initial_condition(stmg_handle* hh, double* V0) {
+stmg_status stmg_initial_condition(stmg_handle* hh, stmg_field_fn v0, void* user, double* V0) {
   if (!hh) return STMG_ERR_ARG;
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!V0) return h->fail(STMG_ERR_ARG, "stmg_initial_condition: null pointer");
+  if (v0) {
+    // the caller's v0 at the velocity nodes of the finest level (GLL nodes of the mapped cells)
+    const Level& L = h->levels[0];
+    const int d = L.d, n = L.n, r1 = L.r + 1;
+    const int64_t nn = L.nnodes;
+    std::vector<double> xs((size_t)d * nn), out((size_t)d * nn, 0.0);
+    for (int64_t gi = 0; gi < nn; ++gi) {
+      int64_t rem = gi;
+      int cc[3] = {0, 0, 0};
+      double xh[3] = {0, 0, 0};
+      for (int l = 0; l < d; ++l) {
+        const int gm = (int)(rem % L.N1); rem /= L.N1;
+        cc[l] = std::min(gm / r1, n - 1);
+        xh[l] = L.tabs.gll[gm - cc[l] * r1];
+      }
+      double x[3] = {0, 0, 0};
+      for (int c = 0; c < (1 << d); ++c) {
+        double wgt = 1.0;
+        int64_t v = 0, s = 1;
+        for (int l = 0; l < d; ++l) {
+          const int b = (c >> l) & 1;
+          wgt *= b ? xh[l] : 1.0 - xh[l];
+          v += (int64_t)(cc[l] + b) * s;
+          s *= (n + 1);
+        }
+        for (int i = 0; i < d; ++i) x[i] += h->verts0[v * d + i] * wgt;
+      }
+      for (int i = 0; i < d; ++i) xs[(size_t)i * nn + gi] = x[i];
+    }
+    v0(user, nn, xs.data(), 0.0, out.data());
+    for (double v : out)
+      if (!std::isfinite(v)) return h->fail(STMG_ERR_NUMERIC, "stmg_initial_condition: v0 returned a non-finite value");
+    try {
+      h->upload(V0, out.data(), out.size() * sizeof(double));
+    } catch (const CudaFailure& f) {
+      return h->fail(STMG_ERR_CUDA, std::string("stmg_initial_condition: ") + cudaGetErrorString(f.err));
+    }
+    return STMG_OK;
+  }
+  if (h->pb.problem == STMG_USER) {
+    cudaError_t e = cudaMemsetAsync(V0, 0, h->levels[0].Nv * sizeof(double), h->stream);
+    if (e != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string("stmg_initial_condition: ") + cudaGetErrorString(e));
+    return STMG_OK;
+  }
   cudaError_t e = launch_initial_condition(h->levels[0], h->pb, V0, h->stream);
   if (e != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string("stmg_initial_condition: ") + cudaGetErrorString(e));
   return STMG_OK;

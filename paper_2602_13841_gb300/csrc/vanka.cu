@@ -4,6 +4,7 @@
 #include "mg.hpp"
 #include "op_launch.cuh"
 #include "vanka.cuh"
+#include "vanka_diag.cuh"
 #include "vec.cuh"
 #include "counters.hpp"
 
@@ -55,9 +56,16 @@ static bool apply_onchip(const Level& lv, size_t es_store, size_t es) {
   return apply_slot_bytes(lv.k + 1, (int)vanka_spatial_size(lv), es_store, es) <= 227 * 1024;
 }
 
+// Shared memory of k_patch_diag: inverse temporal blocks, Schur complement, pivots, column.
+static size_t patch_diag_smem(const Level& lv, size_t es) {
+  const size_t mv = vanka_spatial_size(lv) - lv.npc, kp1 = lv.k + 1, ns = kp1 * lv.npc;
+  return es * (mv * kp1 * kp1 + ns * ns + 2 * ns + 2) + sizeof(int) * (ns + 1);
+}
+
 bool vanka_supported(const Level& lv, size_t es) {
   const size_t lim = 227 * 1024;
   const size_t ms = vanka_spatial_size(lv);
+  if (lv.smoother == 1) return elem_smem_any(lv, es) <= lim && patch_diag_smem(lv, es) <= lim;
   return elem_smem_any(lv, es) <= lim && es * 2 * ms + sizeof(int) * ms + 16 <= lim;
 }
 
@@ -81,6 +89,7 @@ size_t vanka_elem_cells(const Level& lv) {
 }
 
 size_t vanka_work_entries(const Level& lv, size_t es) {
+  if (lv.smoother == 1) return 0;
   return patch_onchip(lv, es) ? 0 : (size_t)kWorkSlots * work_slot(lv);
 }
 
@@ -101,7 +110,8 @@ static cudaError_t build_dn(const Level& lv, const Problem& pb, const T* U, T* v
   int64_t ncells = lv.Np / lv.npc;
   int64_t g = (lv.Nv + 255) / 256; if (g > 152 * 8) g = 152 * 8;
   k_midpoint<T><<<(int)g, 256, 0, s>>>(U, vstar, lv.Nv, lv.k + 1, tb);
-  const bool onchip = patch_onchip(lv, sizeof(T));
+  const bool diag = lv.smoother == 1;
+  const bool onchip = diag || patch_onchip(lv, sizeof(T));
   if (!onchip && !work) return cudaErrorInvalidValue;
   VankaArgs<T> V{level_args<T>(lv, pb, 0.0), vstar, EA, EB, EM, 0, inv, (__half*)invh, scale, status,
                  onchip ? nullptr : work, onchip ? 0 : (int64_t)work_slot(lv)};
@@ -109,7 +119,11 @@ static cudaError_t build_dn(const Level& lv, const Problem& pb, const T* U, T* v
   cudaError_t e = allow_smem(k_elem<T, D, N>, es);
   if (e != cudaSuccess) return e;
   size_t ps = 0;
-  if (onchip) {
+  if (diag) {
+    ps = patch_diag_smem(lv, sizeof(T));
+    e = allow_smem(k_patch_diag<T, D, N>, ps);
+    if (e != cudaSuccess) return e;
+  } else if (onchip) {
     ps = patch_smem(lv, sizeof(T));
     e = allow_smem(k_patch<T, D, N>, ps);
     if (e != cudaSuccess) return e;
@@ -129,7 +143,9 @@ static cudaError_t build_dn(const Level& lv, const Problem& pb, const T* U, T* v
     const int64_t p0 = z0 * plane, p1 = z1 * plane;
     V.ebase = e0;
     k_elem<T, D, N><<<(unsigned)(e1 - e0), 256, es, s>>>(V, tb, e0, e1);
-    if (onchip) {
+    if (diag) {
+      k_patch_diag<T, D, N><<<(unsigned)(p1 - p0), 128, ps, s>>>(V, tb, p0, p1);
+    } else if (onchip) {
       // 3D patches (m_s = 85 for Q2/P1): more threads shorten each elimination step
       k_patch<T, D, N><<<(unsigned)(p1 - p0), D == 3 ? 512 : 256, ps, s>>>(V, tb, te, p0, p1);
     } else {
@@ -189,6 +205,18 @@ static cudaError_t apply_dn(const Level& lv, const Problem& pb, const T* inv, co
                             unsigned extra_tx, cudaStream_t s) {
   const ColorInfo& ci = lv.colors[color];
   if (ci.count == 0) return cudaSuccess;
+  if (lv.smoother == 1) {
+    // diagonal space-time Vanka: one warp per cell, four cells per block
+    constexpr int NL = Shape<D, N>::Q;
+    const int cpb = 4;
+    const size_t smem = (size_t)cpb * diag_slot_bytes(D * NL, lv.npc, lv.k + 1, sizeof(T));
+    cudaError_t e = allow_smem(k_vanka_apply_diag<T, D, N>, smem);
+    if (e != cudaSuccess) return e;
+    k_vanka_apply_diag<T, D, N><<<(unsigned)((ci.count + cpb - 1) / cpb), 32 * cpb, smem, s>>>(
+        level_args<T>(lv, pb, 0.0), inv, res, d, (T)omega, (T)omega_p, make_tab<T>(lv.tabs, pb.tau), ci, cpb);
+    note_launch();
+    return cudaGetLastError();
+  }
   cudaError_t e = invh ? apply_cells<T, __half, D, N>(lv, pb, (const __half*)invh, scale, res, d, omega, omega_p, ci,
                                                       wstat, extra_tx, s)
                        : apply_cells<T, T, D, N>(lv, pb, inv, nullptr, res, d, omega, omega_p, ci, wstat, extra_tx,
@@ -200,6 +228,7 @@ static cudaError_t apply_dn(const Level& lv, const Problem& pb, const T* inv, co
 
 size_t vanka_inv_entries(const Level& lv, int es) {
   const size_t ms = vanka_spatial_size(lv);
+  if (lv.smoother == 1) return (size_t)diag_blob_entries((int)(ms - lv.npc), lv.npc, lv.k + 1);
   return (size_t)(lv.k + 1) * ms * (size_t)inv_stride((int)ms, es);
 }
 

@@ -11,7 +11,24 @@ LIBPATH = os.path.join(_HERE, "libstmg.so")
 _lib = None
 
 STMG_FP64, STMG_FP32 = 0, 1
-PROBLEMS = {"TG2D": 0, "MMS2D": 1, "TG3D": 2, "MMS3D": 3, "CAV3D": 4}
+PROBLEMS = {"TG2D": 0, "MMS2D": 1, "TG3D": 2, "MMS3D": 3, "CAV3D": 4, "USER": 5}
+
+# void (*stmg_field_fn)(void* user, int64_t npts, const double* x, double t, double* out)
+FIELD_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                            ctypes.POINTER(ctypes.c_double))
+
+
+def field_callback(func, dim):
+    """Wrap a Python function func(x, t) -> values, x and values numpy arrays of shape (dim, npts),
+    as a stmg_field_fn (None stays NULL).  The wrapper only copies arrays across the boundary."""
+    if func is None:
+        return None
+
+    def cb(user, npts, x, t, out):
+        xs = np.ctypeslib.as_array(x, shape=(dim * npts,)).reshape(dim, npts)
+        vals = np.asarray(func(xs, t), dtype=np.float64).reshape(dim, npts)
+        np.ctypeslib.as_array(out, shape=(dim * npts,))[:] = vals.ravel()
+    return FIELD_FN(cb)
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NOT_CONVERGED",
           5: "ERR_NUMERIC", 6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
 
@@ -39,7 +56,7 @@ class Params(ctypes.Structure):
         ("rebuild_kappa_abs", ctypes.c_int),
         ("stag_s", ctypes.c_int), ("stag_theta", ctypes.c_double),
         ("omega_p", ctypes.c_double), ("vanka_fp16", ctypes.c_int), ("build_chunk_cells", ctypes.c_int),
-        ("keep_time_degree", ctypes.c_int),
+        ("keep_time_degree", ctypes.c_int), ("smoother", ctypes.c_int),
     ]
 
 
@@ -73,7 +90,8 @@ def load():
         "stmg_level_info": (I, [P, I, Ip, Ip, Ip, I64p, I64p, I64p]),
         "stmg_apply": (I, [P, I, I, V, V, V]),
         "stmg_residual": (I, [P, D, V, V, V]),
-        "stmg_initial_condition": (I, [P, V]),
+        "stmg_initial_condition": (I, [P, P, P, V]),
+        "stmg_set_data": (I, [P, P, P, P]),
         "stmg_initial_guess": (I, [P, V, V]),
         "stmg_mass": (I, [P, V, V]),
         "stmg_smoother_build": (I, [P, V]),
@@ -193,10 +211,24 @@ class Solver:
                                            _ptr(Vprev, torch.float64, L["Nv"], "Vprev"),
                                            _ptr(R, torch.float64, L["Nst"], "R")), "residual")
 
-    def initial_condition(self, V0):
+    def initial_condition(self, V0, v0=None):
+        """V0 <- the initial velocity at the velocity nodes: the problem's own, or v0(x, t) given as
+        a Python function of (dim, npts) coordinates (evaluated on the host by the library)."""
         import torch
-        self._check(self.lib.stmg_initial_condition(self.h, _ptr(V0, torch.float64, self.levels[0]["Nv"], "V0")),
+        cb = field_callback(v0, self.params.dim)
+        self._check(self.lib.stmg_initial_condition(self.h, ctypes.cast(cb, ctypes.c_void_p) if cb else None, None,
+                                                    _ptr(V0, torch.float64, self.levels[0]["Nv"], "V0")),
                     "initial_condition")
+
+    def set_data(self, f=None, g=None):
+        """Problem data from the caller (problem STMG_USER): body force f(x, t) and Dirichlet data
+        g(x, t), Python functions of (dim, npts) coordinates returning (dim, npts) values; None is a
+        zero field.  The callbacks stay referenced by the Solver while the handle may call them."""
+        self._cb = (field_callback(f, self.params.dim), field_callback(g, self.params.dim))
+        fp = ctypes.cast(self._cb[0], ctypes.c_void_p) if self._cb[0] else None
+        gp = ctypes.cast(self._cb[1], ctypes.c_void_p) if self._cb[1] else None
+        self._check(self.lib.stmg_set_data(self.h, fp, gp, None), "set_data")
+        self.params.problem = PROBLEMS["USER"]
 
     # -------------------------------------------------------------- solver
     @property

@@ -131,3 +131,42 @@ def test_midpoint_state_is_the_field_at_the_slab_midpoint(k):
         U[a * Nv:(a + 1) * Nv] = sum(coef[j] * t ** j for j in range(k + 1))
     got = multigrid.midpoint_velocity(lvl, U)
     assert np.abs(got - coef[0]).max() < 1e-13
+
+
+def test_diagonal_vanka_patch_is_the_spatially_diagonal_surrogate():
+    """DiagonalVanka's local solve equals the dense solve of the surrogate patch whose velocity block
+    is replaced by K (x) diag(M) + W (x) diag(A) (brute-force A, M; textbook DG(1) time matrices),
+    with the pressure coupling kept whole; and it differs from the full patch."""
+    n, r, k, nu, tau, omega = 2, 1, 1, 0.03, 0.2, 0.3
+    that = np.array([-1.0 / 3.0, 1.0])
+    K = np.array([[9 / 8, 3 / 8], [-9 / 8, 5 / 8]])
+    w = 0.5 * tau * np.array([1.5, 0.5])
+    X, Y = _nodes_xy(n, r)
+    f0, f1 = _affine(X, Y, F0), _affine(X, Y, F1)
+    Va = [np.concatenate([(f0 + t * f1)[:, 0], (f0 + t * f1)[:, 1]]) for t in that]
+    vstar = np.concatenate([f0[:, 0], f0[:, 1]])
+    As, B, Ms = _brute_force_operator(n, r, nu, vstar, 10.0, 10.0, with_mass=True)
+    Jt = _slab_matrix(K, w, Ms, [As, As], B)
+    lvl = multigrid.Level(2, n, r, k, uniform_vertices(2, n), tau, nu)
+    U = np.zeros(lvl.Nst)
+    U[:2 * Ms.shape[0]] = np.concatenate(Va)
+    dv = multigrid.DiagonalVanka(lvl, U, omega, 1.0)
+    full = multigrid.Vanka(lvl, U, omega, 1.0)
+    rng = np.random.default_rng(3)
+    import scipy.linalg as sla
+    for (idx, lu), (_, lu_full) in zip(dv.patches, full.patches):
+        S = Jt[np.ix_(idx, idx)]
+        nv = (k + 1) * 2 * (r + 2) ** 2                    # patch velocity DoFs
+        ms_v = 2 * (r + 2) ** 2
+        Sd = S.copy()
+        for p in range(nv):
+            for q in range(nv):
+                if p % ms_v != q % ms_v:
+                    Sd[p, q] = 0.0
+        # the kept entries are K_ab M_ii + delta_ab w_a A_ii
+        a0, i0 = 0, 3
+        assert abs(Sd[i0, ms_v + i0] - K[0, 1] * Ms[idx[i0], idx[i0]]) < 1e-14 * abs(Sd).max()
+        b = rng.uniform(-1, 1, len(idx))
+        want = np.linalg.solve(Sd, b)
+        assert np.abs(sla.lu_solve(lu, b) - want).max() < 1e-11 * np.abs(want).max()
+        assert np.abs(sla.lu_solve(lu_full, b) - want).max() > 1e-6 * np.abs(want).max()
