@@ -205,8 +205,12 @@ class Vanka:
         self.patches = []
         for c in range(level.space.mesh.ncells):
             idx = patch_dofs(level, c)
-            S = Jt[idx][:, idx].toarray()
+            S = self.patch_matrix(Jt[idx][:, idx].toarray())
             self.patches.append((idx, sla.lu_factor(S)))
+
+    def patch_matrix(self, S):
+        """The local matrix whose inverse the sweep applies: the surrogate patch itself."""
+        return S
 
     def sweep(self, J, rhs, d):
         """d <- d + W sum_K R_K^T S~_K^{-1} R_K (rhs - J d) (Eq. vanka0); W = omega on velocity
@@ -229,21 +233,13 @@ class DiagonalVanka(Vanka):
     The patch ordering is that of patch_dofs: velocity [time node][component][node], then
     pressure; spatial velocity DoF of a patch row = its position modulo d * nloc."""
 
-    def __init__(self, level, U, omega, omega_p=None):
-        super().__init__(level, U, omega, omega_p)
-        vstar = midpoint_velocity(level, U)
-        Jt = forms.jacobian(level.space, level.td, U, level.nu, *level.gamma, level.bconv, vstar=vstar,
-                            hscale=level.hscale).tocsr()
-        ms_v = level.d * level.space.nloc
-        nvp = (level.k + 1) * ms_v
+    def patch_matrix(self, S):
+        ms_v = self.level.d * self.level.space.nloc
+        nvp = (self.level.k + 1) * ms_v
         sid = np.arange(nvp) % ms_v
-        keep = sid[:, None] == sid[None, :]
-        self.patches = []
-        for c in range(level.space.mesh.ncells):
-            idx = patch_dofs(level, c)
-            S = Jt[idx][:, idx].toarray()
-            S[:nvp, :nvp] *= keep
-            self.patches.append((idx, sla.lu_factor(S)))
+        S = S.copy()
+        S[:nvp, :nvp] *= sid[:, None] == sid[None, :]
+        return S
 
 
 class CoarseSolver:

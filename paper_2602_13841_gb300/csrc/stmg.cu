@@ -192,14 +192,21 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
         tot += cells * es * (mv * (lk + 1.0) * (lk + 1.0) + npc * mv + (lk + 1.0) * npc * (lk + 1.0) * npc);
       else
         tot += p->vanka_fp16 ? cells * (ent * 2.0 + 4.0 * (lk + 1.0)) : cells * ent * es;  // patch inverses
-      // element-matrix scratch: chunks of cell planes, at most ~2^18 cells (three planes at least)
-      const double plane = cells / ln, cap = p->build_chunk_cells > 0 ? (double)p->build_chunk_cells : 262144.0;
+      // element-matrix scratch: chunks of cell planes, at most ~2^18 cells and 8 GiB of FP64
+      // element matrices (three planes at least)
+      const double plane = cells / ln;
+      double cap = p->build_chunk_cells > 0 ? (double)p->build_chunk_cells : 262144.0;
+      cap = std::min(cap, std::floor(8.0 * 1073741824.0 / (8.0 * (mv * mv + npc * mv + nl * nl))));
       const double ec = cells <= cap ? cells : std::min(cells, std::max(3.0, std::floor(cap / plane)) * plane);
       ea = std::max(ea, ec * mv * mv); eb = std::max(eb, ec * npc * mv); em = std::max(em, ec * nl * nl);
       // patches beyond shared memory are factorised in a global workspace of 304 block slots
       const double pslot = 2.0 * msp * msp + mv * mv + nl * nl;
       if (p->smoother != 1 && es * (pslot + 2.0 * msp) + 4.0 * msp + 16.0 > 227.0 * 1024.0)
         wk = std::max(wk, 304.0 * pslot * es);
+      // element tables beyond shared memory (3D Q4/P3) use 304 slots of the same workspace
+      const double nf = std::pow(lr + 2.0, d - 1);
+      const double etab = nl * nl * d + nl * nl + nl + nl * d + d * nl + d * (nf * (2.0 + 2.0 * d) + 2.0 * nf * nl) + 32.0;
+      if (es * etab > 227.0 * 1024.0) wk = std::max(wk, 304.0 * etab * es);
       nvmax = std::max(nvmax, Nv);
       tot += 3.0 * std::max((lk + 1.0) * Nv, (lk + 1.0) * Np) * es;      // transfer scratch
     }

@@ -62,11 +62,20 @@ static size_t patch_diag_smem(const Level& lv, size_t es) {
   return es * (mv * kp1 * kp1 + ns * ns + 2 * ns + 2) + sizeof(int) * (ns + 1);
 }
 
+// The per-cell tables of the element-matrix kernel fit shared memory (else k_elem_global).
+static bool elem_onchip(const Level& lv, size_t es) { return elem_smem_any(lv, es) <= 227 * 1024; }
+
+static size_t elem_table_any(const Level& lv) {
+  int N = lv.r + 2;
+  if (lv.d == 2) return N == 3 ? elem_table_entries<2, 3>() : N == 4 ? elem_table_entries<2, 4>() : elem_table_entries<2, 5>();
+  return N == 3 ? elem_table_entries<3, 3>() : N == 4 ? elem_table_entries<3, 4>() : elem_table_entries<3, 5>();
+}
+
 bool vanka_supported(const Level& lv, size_t es) {
   const size_t lim = 227 * 1024;
   const size_t ms = vanka_spatial_size(lv);
-  if (lv.smoother == 1) return elem_smem_any(lv, es) <= lim && patch_diag_smem(lv, es) <= lim;
-  return elem_smem_any(lv, es) <= lim && es * 2 * ms + sizeof(int) * ms + 16 <= lim;
+  if (lv.smoother == 1) return patch_diag_smem(lv, es) <= lim;
+  return es * 2 * ms + sizeof(int) * ms + 16 <= lim;
 }
 
 // Block slots of the global build workspace and their size in entries.
@@ -79,18 +88,24 @@ static size_t work_slot(const Level& lv) {
   return 2 * ms * ms + mv * mv + nl * nl;
 }
 
-// Cells whose element matrices the build scratch holds at once (whole level if smaller).
+// Cells whose element matrices the build scratch holds at once (whole level if smaller): at most
+// chunk_cells cells and at most 8 GiB of FP64 element matrices (3D Q4/P3: 1.3 MB per cell).
 size_t vanka_elem_cells(const Level& lv) {
   const size_t ncells = lv.Np / lv.npc, plane = ncells / lv.n;
-  const size_t cap = (size_t)lv.chunk_cells;
+  size_t nl = 1;
+  for (int l = 0; l < lv.d; ++l) nl *= (lv.r + 2);
+  const size_t mv = lv.d * nl, per = 8 * (mv * mv + (size_t)lv.npc * mv + nl * nl);
+  size_t cap = (size_t)lv.chunk_cells;
+  if (cap * per > ((size_t)8 << 30)) cap = ((size_t)8 << 30) / per;
   if (ncells <= cap) return ncells;
   const size_t planes = cap / plane > 3 ? cap / plane : 3;     // a chunk plus its two halo planes
   return planes * plane < ncells ? planes * plane : ncells;
 }
 
 size_t vanka_work_entries(const Level& lv, size_t es) {
-  if (lv.smoother == 1) return 0;
-  return patch_onchip(lv, es) ? 0 : (size_t)kWorkSlots * work_slot(lv);
+  const size_t pw = (lv.smoother == 1 || patch_onchip(lv, es)) ? 0 : (size_t)kWorkSlots * work_slot(lv);
+  const size_t ew = elem_onchip(lv, es) ? 0 : (size_t)kWorkSlots * elem_table_any(lv);
+  return pw > ew ? pw : ew;
 }
 
 // v* = sum_a phi_a(t*) V^a
@@ -112,12 +127,16 @@ static cudaError_t build_dn(const Level& lv, const Problem& pb, const T* U, T* v
   k_midpoint<T><<<(int)g, 256, 0, s>>>(U, vstar, lv.Nv, lv.k + 1, tb);
   const bool diag = lv.smoother == 1;
   const bool onchip = diag || patch_onchip(lv, sizeof(T));
-  if (!onchip && !work) return cudaErrorInvalidValue;
+  const bool eon = elem_onchip(lv, sizeof(T));
+  if ((!onchip || !eon) && !work) return cudaErrorInvalidValue;
   VankaArgs<T> V{level_args<T>(lv, pb, 0.0), vstar, EA, EB, EM, 0, inv, (__half*)invh, scale, status,
                  onchip ? nullptr : work, onchip ? 0 : (int64_t)work_slot(lv)};
   size_t es = elem_smem<D, N>(sizeof(T));
-  cudaError_t e = allow_smem(k_elem<T, D, N>, es);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (eon) {
+    e = allow_smem(k_elem<T, D, N>, es);
+    if (e != cudaSuccess) return e;
+  }
   size_t ps = 0;
   if (diag) {
     ps = patch_diag_smem(lv, sizeof(T));
@@ -142,7 +161,16 @@ static cudaError_t build_dn(const Level& lv, const Problem& pb, const T* U, T* v
     const int64_t e0 = (z0 > 0 ? z0 - 1 : 0) * plane, e1 = (z1 < lv.n ? z1 + 1 : lv.n) * plane;
     const int64_t p0 = z0 * plane, p1 = z1 * plane;
     V.ebase = e0;
-    k_elem<T, D, N><<<(unsigned)(e1 - e0), 256, es, s>>>(V, tb, e0, e1);
+    if (eon) {
+      k_elem<T, D, N><<<(unsigned)(e1 - e0), 256, es, s>>>(V, tb, e0, e1);
+    } else {
+      // tables in global memory: one slot per block (the slots precede any patch workspace use,
+      // which follows on the same stream)
+      VankaArgs<T> Ve = V;
+      Ve.work = work;
+      const int64_t grid = e1 - e0 < kWorkSlots ? e1 - e0 : kWorkSlots;
+      k_elem_global<T, D, N><<<(unsigned)grid, 256, 0, s>>>(Ve, tb, e0, e1);
+    }
     if (diag) {
       k_patch_diag<T, D, N><<<(unsigned)(p1 - p0), 128, ps, s>>>(V, tb, p0, p1);
     } else if (onchip) {
@@ -165,7 +193,7 @@ cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar
   const int N = lv.r + 2;
 #define STMG_B(DD, NN) return build_dn<T, DD, NN>(lv, pb, U, vstar, EA, EB, EM, inv, invh, scale, status, work, s)
   if (lv.d == 2) { if (N == 3) STMG_B(2, 3); if (N == 4) STMG_B(2, 4); if (N == 5) STMG_B(2, 5); }
-  else { if (N == 3) STMG_B(3, 3); if (N == 4) STMG_B(3, 4); }
+  else { if (N == 3) STMG_B(3, 3); if (N == 4) STMG_B(3, 4); if (N == 5) STMG_B(3, 5); }
 #undef STMG_B
   return cudaErrorNotSupported;
 }
@@ -206,10 +234,12 @@ static cudaError_t apply_dn(const Level& lv, const Problem& pb, const T* inv, co
   const ColorInfo& ci = lv.colors[color];
   if (ci.count == 0) return cudaSuccess;
   if (lv.smoother == 1) {
-    // diagonal space-time Vanka: one warp per cell, four cells per block
+    // diagonal space-time Vanka: one warp per cell, up to four cells per block
     constexpr int NL = Shape<D, N>::Q;
-    const int cpb = 4;
-    const size_t smem = (size_t)cpb * diag_slot_bytes(D * NL, lv.npc, lv.k + 1, sizeof(T));
+    const size_t slot = diag_slot_bytes(D * NL, lv.npc, lv.k + 1, sizeof(T));
+    int cpb = 4;
+    while (cpb > 1 && (size_t)cpb * slot > 200 * 1024) --cpb;
+    const size_t smem = (size_t)cpb * slot;
     cudaError_t e = allow_smem(k_vanka_apply_diag<T, D, N>, smem);
     if (e != cudaSuccess) return e;
     k_vanka_apply_diag<T, D, N><<<(unsigned)((ci.count + cpb - 1) / cpb), 32 * cpb, smem, s>>>(
@@ -239,7 +269,7 @@ cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const 
   const int N = lv.r + 2;
 #define STMG_A(DD, NN) return apply_dn<T, DD, NN>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, wstat, extra_tx, s)
   if (lv.d == 2) { if (N == 3) STMG_A(2, 3); if (N == 4) STMG_A(2, 4); if (N == 5) STMG_A(2, 5); }
-  else { if (N == 3) STMG_A(3, 3); if (N == 4) STMG_A(3, 4); }
+  else { if (N == 3) STMG_A(3, 3); if (N == 4) STMG_A(3, 4); if (N == 5) STMG_A(3, 5); }
 #undef STMG_A
   return cudaErrorNotSupported;
 }

@@ -80,14 +80,14 @@ __device__ inline void node_multi(int i, int* im) {
 }
 
 // ---------------------------------------------------------------------------- element matrices
+// Element matrices of one cell, computed by the whole block.  `sm` holds the per-cell tables
+// (shared memory, or for cells whose tables exceed it a per-block slot of global memory).
 template <typename T, int D, int N>
-__global__ void k_elem(VankaArgs<T> V, Tab<T> tb, int64_t c0, int64_t c1) {
+__device__ void elem_cell(const VankaArgs<T>& V, const Tab<T>& tb, int64_t cell, T* sm) {
   constexpr int Q = Shape<D, N>::Q;
   constexpr int NL = Q;                  // local nodes per component (N = n_q)
   constexpr int NF = Shape<D, N>::NF;
   constexpr int MV = D * NL;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
   T* s_gphi = sm;                        // [Q][NL][D] physical basis gradients
   T* s_phi = s_gphi + Q * NL * D;        // [Q][NL]
   T* s_jxw = s_phi + Q * NL;             // [Q]
@@ -100,8 +100,6 @@ __global__ void k_elem(VankaArgs<T> V, Tab<T> tb, int64_t c0, int64_t c1) {
   __shared__ int s_faces[6];
   __shared__ int s_nf;
 
-  const int64_t cell = c0 + blockIdx.x;
-  if (cell >= c1) return;
   const LevelArgs<T>& L = V.L;
   int cc[3] = {0, 0, 0};
   cell_coords<D>(cell, L.n, cc);
@@ -270,6 +268,33 @@ __global__ void k_elem(VankaArgs<T> V, Tab<T> tb, int64_t c0, int64_t c1) {
     T acc = 0;
     for (int q = 0; q < Q; ++q) acc += s_jxw[q] * s_phi[q * NL + i] * s_phi[q * NL + j];
     EM[ent] = acc;
+  }
+}
+
+// Entries of the per-cell tables of elem_cell.
+template <int D, int N>
+__host__ __device__ constexpr size_t elem_table_entries() {
+  return (size_t)Shape<D, N>::Q * Shape<D, N>::Q * D + (size_t)Shape<D, N>::Q * Shape<D, N>::Q + Shape<D, N>::Q +
+         (size_t)Shape<D, N>::Q * D + (size_t)D * Shape<D, N>::Q +
+         (size_t)D * (Shape<D, N>::NF * (2 + 2 * D) + 2 * (size_t)Shape<D, N>::NF * Shape<D, N>::Q) + 8 + 24;
+}
+
+template <typename T, int D, int N>
+__global__ void k_elem(VankaArgs<T> V, Tab<T> tb, int64_t c0, int64_t c1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t cell = c0 + blockIdx.x;
+  if (cell >= c1) return;
+  elem_cell<T, D, N>(V, tb, cell, reinterpret_cast<T*>(smem_raw));
+}
+
+// Cells whose tables exceed shared memory (3D Q4/P3): the tables live in a per-block slot of the
+// global workspace V.work (elem_table_entries entries per slot); blocks stride over the cells.
+template <typename T, int D, int N>
+__global__ void k_elem_global(VankaArgs<T> V, Tab<T> tb, int64_t c0, int64_t c1) {
+  T* sm = V.work + (int64_t)blockIdx.x * (int64_t)elem_table_entries<D, N>();
+  for (int64_t cell = c0 + blockIdx.x; cell < c1; cell += gridDim.x) {
+    elem_cell<T, D, N>(V, tb, cell, sm);
+    __syncthreads();
   }
 }
 

@@ -74,6 +74,8 @@ def test_transfers_match_oracle(d, n, r, k, amp, prec):
                                                    (3, 4, 1, 1, 0.1, "fp32", 0),
                                                    # 3D Q3/P2: patches beyond shared memory (global path)
                                                    (3, 2, 2, 1, 0.1, "fp64", 0), (3, 4, 2, 1, 0.0, "fp32", 0),
+                                                   # 3D Q4/P3: element tables and patches in global memory
+                                                   (3, 2, 3, 1, 0.1, "fp64", 0), (3, 2, 3, 0, 0.0, "fp32", 0),
                                                    # p-coarsening in space only, DG(k) on every level
                                                    (2, 8, 2, 2, 0.15, "fp64", 1), (3, 4, 1, 2, 0.1, "fp32", 1)])
 def test_smoother_and_vcycle_match_oracle(d, n, r, k, amp, prec, keep):
@@ -123,6 +125,7 @@ def test_smoother_and_vcycle_match_oracle(d, n, r, k, amp, prec, keep):
     ("fp32", 3, 4, 1, 2, 0.1, 1.0 / 400, 0.01, "MMS3D"),   # small case of the 3D Q2/P1/DG(2) workload
     ("fp32", 3, 4, 2, 1, 0.0, 1.0 / 1600, 0.02, "TG3D"),   # small case of the 3D Q3/P2/DG(1) workload
     ("fp32", 3, 4, 2, 2, 0.0, 4e-4, 1.0 / 32, "CAV3D"),    # small case of the lid-driven cavity (Sec. 5.2)
+    ("fp32", 3, 2, 3, 1, 0.1, 1.0 / 400, 0.05, "TG3D"),    # 3D Q4/P3 (global-memory element tables)
     ("fp32+keep", 2, 8, 2, 2, 0.1, 1e-3, 0.05, "TG2D"),    # p-coarsening in space only
 ])
 def test_slab_solve_reaches_tolerance_and_matches_exact_solution(precision, d, n, r, k, amp, nu, tau, pname):
@@ -225,7 +228,7 @@ def test_chunked_smoother_build_equals_single_chunk(d, n, r, k, prec):
 
 @pytest.mark.parametrize("d,n,r,k,amp,prec", [(2, 8, 2, 2, 0.15, "fp64"), (2, 6, 1, 1, 0.0, "fp64"),
                                               (2, 7, 2, 0, 0.1, "fp32"), (3, 4, 1, 1, 0.1, "fp64"),
-                                              (3, 4, 2, 1, 0.1, "fp32")])
+                                              (3, 4, 2, 1, 0.1, "fp32"), (3, 2, 3, 2, 0.1, "fp64")])
 def test_diagonal_vanka_sweeps_match_oracle(d, n, r, k, amp, prec):
     """The diagonal space-time Vanka (smoother = 1): sweeps from zero and from a nonzero iterate on
     every smoothed level against the oracle's DiagonalVanka (FP64 1e-9, FP32 2e-3 relative)."""
@@ -259,6 +262,7 @@ def test_diagonal_vanka_sweeps_match_oracle(d, n, r, k, amp, prec):
 @pytest.mark.parametrize("precision,d,n,r,k,amp,nu,tau,pname", [
     ("fp32", 2, 8, 2, 2, 0.1, 1e-3, 0.05, "TG2D"),
     ("fp32", 3, 4, 2, 1, 0.0, 1.0 / 1600, 0.02, "TG3D"),
+    ("fp32", 3, 2, 3, 1, 0.1, 1.0 / 400, 0.05, "TG3D"),   # 3D Q4/P3
 ])
 def test_slab_solve_with_diagonal_vanka(precision, d, n, r, k, amp, nu, tau, pname):
     """The slab solve with the diagonal smoother reaches the Newton tolerance and the exact discrete
