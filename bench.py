@@ -52,9 +52,12 @@ WORKLOAD_NAME = ("2D unit square 256x256 mapped (amp 0.1h, seed 1234), Q3/P2disc
 # ||R||_M after 6, 7, 8 steps = 9.1e-18, 6.5e-19, 1.04e-19 (5.9e-12 relative) and still falling, so
 # the FP64 residual resolves the 1e-10 relative target (1.77e-18) with room to spare.
 ATOL = 0.0
-# Smoother of both arms: omega = 1.2 / 2^d (library default), pressure relaxation 1, five pre-
-# and five post-sweeps per level (the lowest time to the Newton tolerance on this workload).
-SMOOTH = dict(nu1=5, nu2=5, omega_p=1.0)
+# Smoother of both arms: omega = 1.2 / 2^d (library default), pressure relaxation 1, two pre- and
+# post-sweeps per level and twelve on the level whose time degree is coarsened next (DG(2) ->
+# DG(1)); the lowest time to 1e-10 relative on this workload among the sweep counts measured
+# (nu/nu_tc = 5/5: 2508 ms per slab, 8/8: 2202, 2/8: 2053, 3/10: 2308, 2/12: 1691, 3/12: 1717,
+# 2/14: 1783, 2/20: 1948).
+SMOOTH = dict(nu1=2, nu2=2, omega_p=1.0)
 # Other workloads (`--workload`, profiling and scaling runs; the headline is "2d"):
 #   3d: 3D unit cube 128^3 mapped, Q2/P1disc (r=1), DG(2), dt=0.01, Re=400 manufactured solution,
 #       FGMRES restart 30, one pre- and post-sweep, FP16 patch storage from 96^3 cells (memory).
@@ -63,10 +66,15 @@ SMOOTH = dict(nu1=5, nu2=5, omega_p=1.0)
 #       second column), the paper's Newton tolerances 1e-8 relative and 1e-12 absolute, FGMRES
 #       capped at 50; K steps march the first K slabs from t = 0.
 WORKLOADS = {
-    "2d": dict(WORKLOAD, name=WORKLOAD_NAME, smooth=5, restart=50, oracle_n=8, rtol=1e-10, atol=ATOL),
+    "2d": dict(WORKLOAD, name=WORKLOAD_NAME, smooth=2, smooth_tc=12, restart=50, oracle_n=8, rtol=1e-10, atol=ATOL),
     "3d": dict(d=3, n=128, r=1, k=2, amp=0.1, seed=1234, nu=1.0 / 400, tau=0.01, problem="MMS3D",
                name=("3D unit cube 128^3 mapped (amp 0.1h, seed 1234), Q2/P1disc (r=1), DG(2), dt=0.01, "
                      "Re=400 manufactured solution; FP32 hp-STMG in FP64 Newton-FGMRES (restart 30)"),
+               smooth=1, restart=30, oracle_n=2, rtol=1e-10, atol=ATOL),
+    "c3": dict(d=3, n=64, r=2, k=1, amp=0.0, seed=2024, nu=1.0 / 1600, tau=0.02, problem="TG3D", noise=0.01,
+               name=("3D unit cube 64^3 Cartesian, Q3/P2disc (r=2), DG(1), dt=0.02, Re=1600 Taylor-Green vortex "
+                     "initial field plus seeded 1% uniform velocity perturbation at interior nodes (seed 2024); "
+                     "FP32 hp-STMG in FP64 Newton-FGMRES (restart 30), 1e-10 relative"),
                smooth=1, restart=30, oracle_n=2, rtol=1e-10, atol=ATOL),
     "cavity3d": dict(d=3, n=16, r=2, k=2, amp=0.0, seed=0, nu=4e-4, tau=8.0 / 256, problem="CAV3D",
                      name=("3D lid-driven cavity [0,1]^3 x [0,8], c=4: 16^3 uniform cells, 256 slabs of "
@@ -139,11 +147,11 @@ def _cpu_model():
     return "unknown"
 
 
-def oracle_child(n, smooth, workload):
+def oracle_child(n, smooth, workload, smooth_tc=0):
     """Time the oracle sample in a child process (fresh interpreter, one BLAS thread): returns
     the cpu_baseline object."""
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-child", "--workload", workload,
-           "--ref-n", str(n), "--smooth", str(smooth)]
+           "--ref-n", str(n), "--smooth", str(smooth), "--smooth-tc", str(smooth_tc)]
     res = subprocess.run(cmd, capture_output=True, text=True, timeout=1800)
     if res.returncode != 0:
         return {"value": None, "unit": "DoF/s", "kind": "oracle", "error": res.stderr.strip()[-300:]}
@@ -159,7 +167,7 @@ def _host_cores():
         return os.cpu_count() or 1
 
 
-def oracle_sample(n=16, slabs=1, smooth=SMOOTH["nu1"], w=None):
+def oracle_sample(n=16, slabs=1, smooth=SMOOTH["nu1"], w=None, smooth_tc=0):
     """FP64 CPU oracle slab solves on a bounded sample: the workload's (d, r, k, dt, Re, mesh
     recipe) on an n x n mesh.  Returns (DoF/s, seconds, N_st, description)."""
     from oracle import forms, krylov, problems
@@ -168,7 +176,7 @@ def oracle_sample(n=16, slabs=1, smooth=SMOOTH["nu1"], w=None):
     prob = problems.make(w["problem"], w["nu"])
     verts = inputs.vertices(w["d"], n, w["amp"], w["seed"])
     S = krylov.SlabSolver(w["d"], n, w["r"], w["k"], verts, w["tau"], prob, rtol=w.get("rtol", 1e-10),
-                          atol=w.get("atol", ATOL),
+                          atol=w.get("atol", ATOL), nu_tc=smooth_tc,
                           **dict(SMOOTH, nu1=smooth, nu2=smooth))
     L = S.L
     Vprev = forms.interpolate_velocity(L.space, prob.v0)
@@ -189,11 +197,12 @@ def run_reference(args):
         return
     W = WORKLOADS[args.workload]
     for _ in range(args.warmup):
-        oracle_sample(n=min(4, W["oracle_n"]), smooth=args.smooth, w=W)
+        oracle_sample(n=min(4, W["oracle_n"]), smooth=args.smooth, w=W, smooth_tc=args.smooth_tc)
     vals = []
     t_tot = 0.0
     for _ in range(args.steps):
-        v, dt, nst, desc = oracle_sample(n=args.ref_n or W["oracle_n"], smooth=args.smooth, w=W)
+        v, dt, nst, desc = oracle_sample(n=args.ref_n or W["oracle_n"], smooth=args.smooth, w=W,
+                                         smooth_tc=args.smooth_tc)
         vals.append(v)
         t_tot += dt
     value = float(np.mean(vals))
@@ -221,11 +230,17 @@ def main():
     ap.add_argument("--vanka-fp16", type=int, default=-1, help="1: FP16 storage of the patch inverses "
                                                                    "(-1: the workload's choice)")
     ap.add_argument("--smooth", type=int, default=0, help="Vanka pre- and post-sweeps per level (0: the workload's)")
+    ap.add_argument("--smooth-tc", type=int, default=-1,
+                    help="sweeps on the levels whose time degree is coarsened next (-1: the workload's; 0: --smooth)")
+    ap.add_argument("--smoother", type=int, default=0, help="0: surrogate-patch Vanka (Sec. 4.3); 1: diagonal Vanka")
     ap.add_argument("--keep-time-degree", type=int, default=0,
                     help="1: p-coarsen in space only, DG(k) on every level (a variant of the paper's order)")
     ap.add_argument("--levels-h", type=int, default=-1,
                     help="h-coarsenings below the p-levels (-1: down to 2 cells per direction)")
     ap.add_argument("--no-op-apply", action="store_true", help="skip the operator apply timing")
+    ap.add_argument("--only-op-apply", action="store_true",
+                    help="profiling runs: time only the finest-level operator applies (FP64, FP32) at the "
+                         "interpolated initial state and print them; no slab solves")
     ap.add_argument("--fp64-precond-steps", type=int, default=2,
                     help="slabs timed with the plain FP64 preconditioner beside the headline (0: skip)")
     ap.add_argument("--variant-smooth", type=int, default=2,
@@ -236,13 +251,16 @@ def main():
     args = ap.parse_args()
     W = WORKLOADS[args.workload]
     if args.oracle_child:
-        v, dt, nst, desc = oracle_sample(n=args.ref_n or W["oracle_n"], smooth=args.smooth or W["smooth"], w=W)
+        v, dt, nst, desc = oracle_sample(n=args.ref_n or W["oracle_n"], smooth=args.smooth or W["smooth"], w=W,
+                                         smooth_tc=args.smooth_tc if args.smooth_tc >= 0 else W.get("smooth_tc", 0))
         print(json.dumps([v, desc]), flush=True)
         return
     if args.n <= 0:
         args.n = W["n"]
     if args.smooth <= 0:
         args.smooth = W["smooth"]
+    if args.smooth_tc < 0:
+        args.smooth_tc = W.get("smooth_tc", 0)
     if args.vanka_fp16 < 0:
         args.vanka_fp16 = 1 if (W["d"] == 3 and args.n >= 96) else 0
     if args.impl == "reference":
@@ -266,6 +284,7 @@ def main():
                             newton_atol=w["atol"], vanka_fp16=int(args.vanka_fp16),
                             gmres_restart=w["restart"], gmres_maxit=w["restart"],
                             keep_time_degree=int(args.keep_time_degree), n_levels_h=int(args.levels_h),
+                            nu_tc=int(args.smooth_tc), smoother=int(args.smoother),
                             **dict(SMOOTH, nu1=args.smooth, nu2=args.smooth))
     stream = torch.cuda.Stream(device=dev)
     S = stmg.Solver(p, inputs.vertices(w["d"], w["n"], w["amp"], w["seed"]), stream=stream.cuda_stream)
@@ -274,8 +293,25 @@ def main():
     with torch.cuda.stream(stream):
         V0 = torch.empty(Nv, dtype=torch.float64, device=dev)
         S.initial_condition(V0)
+        if w.get("noise"):
+            # seeded perturbation of the initial field at the interior velocity nodes:
+            # v0 += noise * max|v0| * U(-1, 1)
+            N1 = (w["r"] + 1) * w["n"] + 1
+            mask = torch.tensor(np.tile(inputs.node_noise_mask(w["d"], N1), w["d"]), device=dev)
+            pert = torch.tensor(inputs.uniform(Nv, w["seed"]), dtype=torch.float64, device=dev)
+            V0 += w["noise"] * float(V0.abs().max()) * pert * mask
         Vp = torch.empty_like(V0)
         U = torch.empty(Nst, dtype=torch.float64, device=dev)
+
+    if args.only_op_apply:
+        with torch.cuda.stream(stream):
+            S.initial_guess(V0, U)
+        torch.cuda.synchronize(dev)
+        op = operator_apply(S, U, stream, dev, w, args, _peaks())
+        S.close()
+        if rank == 0:
+            print(json.dumps({"operator_apply": op, "config": {"workload": W["name"], "n": args.n}}), flush=True)
+        return
 
     def march(nslabs, timed_events=None, stats=None, solver=None):
         Sx = solver or S
@@ -387,7 +423,7 @@ def main():
     variant = None
     if args.variant_smooth > 0 and not args.keep_time_degree:
         pv = stmg.default_params(**{f: getattr(p, f) for f, _ in stmg.Params._fields_})
-        pv.keep_time_degree, pv.nu1, pv.nu2 = 1, args.variant_smooth, args.variant_smooth
+        pv.keep_time_degree, pv.nu1, pv.nu2, pv.nu_tc = 1, args.variant_smooth, args.variant_smooth, 0
         Sv = stmg.Solver(pv, inputs.vertices(w["d"], w["n"], w["amp"], w["seed"]), stream=stream.cuda_stream)
         with torch.cuda.stream(stream):
             march(args.warmup, solver=Sv)
@@ -430,14 +466,18 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            cpu = oracle_child(W["oracle_n"], args.smooth, args.workload)
+            cpu = oracle_child(W["oracle_n"], args.smooth, args.workload, args.smooth_tc)
         line = {
             "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": W["name"] if args.n == W["n"] else W["name"] + " (profiling run: n=%d)" % args.n,
                        "N_st": Nst, "slabs_per_step": 1,
-                       "smoother": {"nu1": args.smooth, "nu2": args.smooth, "omega": "1.2/2^d", "omega_p": 1.0,
+                       "smoother": {"type": ("midpoint-surrogate space-time Vanka (Sec. 4.3)", "diagonal space-time Vanka",
+                                             "exact space-time patches")[args.smoother],
+                                    "nu1": args.smooth, "nu2": args.smooth,
+                                    "nu_time_coarsening_levels": args.smooth_tc or args.smooth,
+                                    "omega": "1.2/2^d", "omega_p": 1.0,
                                     "inverse_storage": "fp16" if args.vanka_fp16 else "fp32"},
                        "coarsening": ("p in space only, DG(k) on every level, then h" if args.keep_time_degree
                                       else "p in space and time ((k,r) -> (k/2,r/2)), then h"),
@@ -491,9 +531,10 @@ def operator_apply(S, U, stream, dev, w, args, peaks, reps=25, warm=5):
         hbm = peaks.get("hbm_gbs", 6800.0)
         out[name] = {"gdof_s": Nst / t / 1e9, "median_ms": t * 1e3, "launches_timed": reps,
                      "algorithmic_bytes": byt, "achieved_gbs": byt / t / 1e9, "hbm_frac": byt / t / 1e9 / hbm}
-    out["note"] = ("FP64: bound by the DFMA pipe (80 % pipe utilisation in the ncu capture), so its HBM "
-                   "fraction is low by construction; FP32: latency-bound (the load-compute-store chain "
-                   "of each lane group at about 44 % warp occupancy)")
+    out["note"] = ("FP64 (colour-split warp kernel): bound by the DFMA pipe (84 % pipe utilisation in the ncu "
+                   "capture), so its HBM fraction is low by construction; FP32 (tiled single-launch kernel): "
+                   "bound by FP32 instruction issue (its FFMA/FMUL/FADD count alone is about 22 M warp "
+                   "instructions per apply at 256^2), so the HBM fraction is capped well below the copy peak")
     return out
 
 

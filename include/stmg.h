@@ -104,7 +104,15 @@ typedef struct {
                           DoF with itself, the pressure coupling stays whole, and the modified patch
                           is solved exactly through its (k+1) C(r+d,d) pressure Schur complement
                           (storage per cell (k+1)^2 m_v + C(r+d,d) m_v + ((k+1) C(r+d,d))^2 reals,
-                          m_v = d (r+2)^d; vanka_fp16 does not apply) */
+                          m_v = d (r+2)^d; vanka_fp16 does not apply).  2: exact space-time patches
+                          R_K J R_K^T, the convection of each time node at its own velocity (the
+                          matrix the surrogate approximates): k+1 element-matrix passes and one
+                          (k+1) m_s square Gauss-Jordan per cell; where the patch fits shared memory
+                          (2D; 3D Q2/P1 with k <= 1), else STMG_ERR_UNSUPPORTED at the build */
+  int nu_tc;           /* > 0: pre- and post-sweeps on the levels whose next coarser level has a
+                          lower time degree (the DG(k) levels of the paper's p-coarsening), in place
+                          of nu1 / nu2 there; <= 0 (default): nu1 / nu2 on every level.  The temporal
+                          modes that DG(k) -> DG(k/2) drops are left to the smoother of those levels */
 } stmg_params;
 
 /* Fill *p with the paper's defaults (Sec. 5, Alg. 1-2) for a d-dimensional problem. */

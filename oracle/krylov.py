@@ -180,9 +180,9 @@ class SlabSolver:
     """Newton-FGMRES with hp-STMG on one configuration (all FP64)."""
 
     def __init__(self, d, n, r, k, vertices, tau, prob, omega=None, max_h=-1, omega_p=1.0, nu1=1, nu2=1,
-                 keep_k=False, smoother="vanka", **overrides):
+                 keep_k=False, smoother="vanka", nu_tc=0, **overrides):
         self.mg = Multigrid(d, n, r, k, vertices, tau, prob.nu, omega=omega, max_h=max_h, omega_p=omega_p,
-                            nu1=nu1, nu2=nu2, keep_k=keep_k, smoother=smoother)
+                            nu1=nu1, nu2=nu2, keep_k=keep_k, smoother=smoother, nu_tc=nu_tc)
         self.L = self.mg.levels[0]
         self.prob = prob
         self.M = forms.slab_mass(self.L.space, self.L.td)

@@ -191,6 +191,8 @@ def patch_dofs(level, cell):
 class Vanka:
     """Cell-wise space-time Vanka with midpoint-surrogate patch matrices (Sec. 4.3)."""
 
+    surrogate = True          # patches of J~ (convection at v*); ExactVanka: patches of J itself
+
     def __init__(self, level, U, omega, omega_p=None):
         self.level, self.omega = level, omega
         self.omega_p = omega if omega_p is None else omega_p
@@ -198,7 +200,7 @@ class Vanka:
         # relaxation per DoF: omega on the (overlapping) velocity DoFs, omega_p on the pressure
         # DoFs, each of which belongs to exactly one patch
         self.weights = np.where(np.arange(level.Nst) < nv, omega, self.omega_p)
-        vstar = midpoint_velocity(level, U)
+        vstar = midpoint_velocity(level, U) if self.surrogate else None
         Jt = forms.jacobian(level.space, level.td, U, level.nu, *level.gamma, level.bconv, vstar=vstar,
                             hscale=level.hscale)
         Jt = Jt.tocsr()
@@ -220,6 +222,14 @@ class Vanka:
         for idx, lu in self.patches:
             upd[idx] += sla.lu_solve(lu, res[idx])
         return d + self.weights * upd
+
+
+class ExactVanka(Vanka):
+    """Space-time Vanka with the exact patch matrices R_K J R_K^T: the convection Jacobian of every
+    time node at that node's own velocity V^a (Eq. JacobianLocal2), the matrix the midpoint
+    surrogate of Sec. 4.3 approximates (the comparison of its Lemma)."""
+
+    surrogate = False
 
 
 class DiagonalVanka(Vanka):
@@ -267,7 +277,7 @@ class Multigrid:
     """hp-STMG V-cycle: z = B^{-1} r on the finest level (Sec. 4.2)."""
 
     def __init__(self, d, n, r, k, vertices, tau, nu, omega=None, nu1=1, nu2=1, omega_p=1.0,
-                 gamma=(10.0, 10.0), bconv=True, max_h=-1, keep_k=False, smoother="vanka"):
+                 gamma=(10.0, 10.0), bconv=True, max_h=-1, keep_k=False, smoother="vanka", nu_tc=0):
         # Eq. vanka0 leaves omega open; the additive sum puts each velocity vertex in up to 2^d
         # patches, so the default damping is 1.2 / 2^d (0.3 in 2D, 0.15 in 3D)
         if omega is None:
@@ -281,8 +291,10 @@ class Multigrid:
             self.P.append(P)
             self.I.append(I)
         self.omega, self.omega_p, self.nu1, self.nu2 = omega, omega_p, nu1, nu2
+        # nu_tc > 0: pre- and post-sweeps on the levels whose next level has a lower time degree
+        self.nu_tc = nu_tc
         # "vanka": the midpoint-surrogate patches of Sec. 4.3; "diagonal": DiagonalVanka
-        self.smoother_cls = {"vanka": Vanka, "diagonal": DiagonalVanka}[smoother]
+        self.smoother_cls = {"vanka": Vanka, "diagonal": DiagonalVanka, "exact": ExactVanka}[smoother]
 
     def level_states(self, U):
         """Velocity state of every level (pressure entries zero) from the fine slab vector."""
@@ -307,11 +319,14 @@ class Multigrid:
         if l == len(self.levels) - 1:
             return self.coarse.solve(r)
         J, sm = self.J[l], self.smoothers[l]
+        nu1, nu2 = self.nu1, self.nu2
+        if self.nu_tc > 0 and self.levels[l + 1].k < self.levels[l].k:
+            nu1 = nu2 = self.nu_tc
         d = np.zeros_like(r)
-        for _ in range(self.nu1):
+        for _ in range(nu1):
             d = sm.sweep(J, r, d)
         rc = self.P[l].T @ (r - J @ d)
         d = d + self.P[l] @ self.vcycle(rc, l + 1)
-        for _ in range(self.nu2):
+        for _ in range(nu2):
             d = sm.sweep(J, r, d)
         return d

@@ -37,7 +37,7 @@ cudaError_t MG<T>::allocate(Handle* hh) {
         }
         size_t nc = lv.Np / lv.npc;
         const size_t ec = vanka_elem_cells(lv);                 // element scratch: one chunk
-        ea = std::max(ea, ec * vanka_elem_size(lv, 0));
+        ea = std::max(ea, ec * vanka_elem_size(lv, 0) * (lv.smoother == 2 ? (size_t)(lv.k + 1) : 1));
         eb = std::max(eb, ec * vanka_elem_size(lv, 1));
         em = std::max(em, ec * vanka_elem_size(lv, 2));
         nv = std::max(nv, (size_t)lv.Nv);
@@ -164,7 +164,7 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
     // per cell: (k+1) m_s^2 stored reals (one spatial inverse per real time eigenvalue, a complex
     // one per conjugate pair), residual gather and d update on the (k+1) m_s patch DoFs
     const double ms = (double)vanka_spatial_size(lv), m = (double)vanka_patch_size(lv);
-    const double ib = lv.smoother == 1 ? (double)vanka_inv_entries(lv, (int)sizeof(T)) * sizeof(T)
+    const double ib = lv.smoother != 0 ? (double)vanka_inv_entries(lv, (int)sizeof(T)) * sizeof(T)
                       : (lv.k + 1) * ms * ms * (invh[l] ? 2.0 : (double)sizeof(T)) + (invh[l] ? 4.0 * (lv.k + 1) : 0.0);
     int64_t cells = 0;
     h->kbegin(KC_VANKA_APPLY);
@@ -185,7 +185,9 @@ cudaError_t MG<T>::vcycle_level(int l, const T* rhs, T* d) {
   if (l == nl - 1) return coarse_solve(rhs, d);
   cudaStream_t s = h->stream;
   const Level& lv = h->levels[l];
-  const int nu1 = h->prm.nu1 > 0 ? h->prm.nu1 : 0, nu2 = h->prm.nu2 > 0 ? h->prm.nu2 : 0;
+  int nu1 = h->prm.nu1 > 0 ? h->prm.nu1 : 0, nu2 = h->prm.nu2 > 0 ? h->prm.nu2 : 0;
+  // levels whose next coarser level has a lower time degree: nu_tc sweeps each way when set
+  if (h->prm.nu_tc > 0 && h->levels[l + 1].k < lv.k) nu1 = nu2 = h->prm.nu_tc;
   if (nu1 > 0) CKE(sweep(l, rhs, d, nu1, true));
   else CKE(cudaMemsetAsync(d, 0, lv.Nst * sizeof(T), s));
   // t = rhs - J d ; r_{l+1} = P^T t

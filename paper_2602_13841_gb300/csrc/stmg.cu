@@ -190,7 +190,12 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
       const double ent = (lk + 1.0) * msp * sti;                         // time-diagonalised inverse
       if (p->smoother == 1)                                              // diagonal blobs
         tot += cells * es * (mv * (lk + 1.0) * (lk + 1.0) + npc * mv + (lk + 1.0) * npc * (lk + 1.0) * npc);
-      else
+      else if (p->smoother == 2) {                                       // whole space-time inverse
+        const double mst = (lk + 1.0) * msp;
+        int stx = (int)mst;
+        while (((long long)mst * stx * (int)es) % 16 != 0) ++stx;
+        tot += cells * mst * stx * es;
+      } else
         tot += p->vanka_fp16 ? cells * (ent * 2.0 + 4.0 * (lk + 1.0)) : cells * ent * es;  // patch inverses
       // element-matrix scratch: chunks of cell planes, at most ~2^18 cells and 8 GiB of FP64
       // element matrices (three planes at least)
@@ -198,7 +203,8 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
       double cap = p->build_chunk_cells > 0 ? (double)p->build_chunk_cells : 262144.0;
       cap = std::min(cap, std::floor(8.0 * 1073741824.0 / (8.0 * (mv * mv + npc * mv + nl * nl))));
       const double ec = cells <= cap ? cells : std::min(cells, std::max(3.0, std::floor(cap / plane)) * plane);
-      ea = std::max(ea, ec * mv * mv); eb = std::max(eb, ec * npc * mv); em = std::max(em, ec * nl * nl);
+      ea = std::max(ea, ec * mv * mv * (p->smoother == 2 ? lk + 1.0 : 1.0));
+      eb = std::max(eb, ec * npc * mv); em = std::max(em, ec * nl * nl);
       // patches beyond shared memory are factorised in a global workspace of 304 block slots
       const double pslot = 2.0 * msp * msp + mv * mv + nl * nl;
       if (p->smoother != 1 && es * (pslot + 2.0 * msp) + 4.0 * msp + 16.0 > 227.0 * 1024.0)
@@ -239,7 +245,7 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
   *out = nullptr;
   if (p->dim < 2 || p->dim > 3 || p->r < 1 || p->r > 3 || p->k < 0 || p->k > 2 ||
       p->n_cells_1d < 1 || p->n_cells_1d > 4096 || !(p->tau > 0) || !(p->nu > 0) ||
-      p->problem < STMG_TG2D || p->problem > STMG_USER || p->smoother < 0 || p->smoother > 1)
+      p->problem < STMG_TG2D || p->problem > STMG_USER || p->smoother < 0 || p->smoother > 2)
     return STMG_ERR_ARG;
   auto h = std::make_unique<Handle>();
   h->prm = *p;
@@ -271,7 +277,7 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
     const double p0 = p->r + 1;
     for (auto& rk : pk) {
       Level lv; lv.d = d; lv.n = n; lv.r = rk.first; lv.k = rk.second;
-      lv.smoother = p->smoother == 1 ? 1 : 0;
+      lv.smoother = p->smoother;
       if (p->build_chunk_cells > 0) lv.chunk_cells = p->build_chunk_cells;
       lv.hscale = 1.0 / (p0 * (p0 + 1.0));
       build_level(h.get(), lv, verts);
@@ -283,7 +289,7 @@ stmg_status stmg_create(const stmg_params* p, const double* vertices, stmg_strea
       cv = coarsen_vertices(cv, d, nn);
       nn /= 2; ++hl;
       Level lv; lv.d = d; lv.n = nn; lv.r = r; lv.k = k;
-      lv.smoother = p->smoother == 1 ? 1 : 0;
+      lv.smoother = p->smoother;
       if (p->build_chunk_cells > 0) lv.chunk_cells = p->build_chunk_cells;
       lv.hscale = ((double)nn / n) / (p0 * (p0 + 1.0));
       build_level(h.get(), lv, cv);

@@ -1,0 +1,12 @@
+// Vanka build and sweep launches for d = 3, float (one translation unit per dimension and element
+// type, compiled in parallel).
+#include "vanka_launch.cuh"
+
+namespace stmg {
+
+template cudaError_t vanka_build_dim<float, 3>(const Level&, const Problem&, const float*, float*, float*, float*, float*, float*,
+                                              void*, float*, int*, float*, cudaStream_t);
+template cudaError_t vanka_apply_dim<float, 3>(const Level&, const Problem&, const float*, const void*, const float*,
+                                              const float*, float*, double, double, int, int*, cudaStream_t, unsigned);
+
+}  // namespace stmg

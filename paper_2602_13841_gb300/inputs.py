@@ -31,6 +31,6 @@ def uniform(size, seed, lo=-1.0, hi=1.0):
 
 def node_noise_mask(d, N1):
     """1.0 at interior velocity nodes of the N1^d grid (x fastest), 0.0 on the boundary."""
-    idx = np.array(list(itertools.product(*([range(N1)] * d))))
-    inner = np.all((idx > 0) & (idx < N1 - 1), axis=1)
+    idx = np.indices((N1,) * d).reshape(d, -1)      # idx[0] slowest; the mask is symmetric in the axes
+    inner = np.all((idx > 0) & (idx < N1 - 1), axis=0)
     return inner.astype(np.float64)

@@ -56,7 +56,7 @@ class Params(ctypes.Structure):
         ("rebuild_kappa_abs", ctypes.c_int),
         ("stag_s", ctypes.c_int), ("stag_theta", ctypes.c_double),
         ("omega_p", ctypes.c_double), ("vanka_fp16", ctypes.c_int), ("build_chunk_cells", ctypes.c_int),
-        ("keep_time_degree", ctypes.c_int), ("smoother", ctypes.c_int),
+        ("keep_time_degree", ctypes.c_int), ("smoother", ctypes.c_int), ("nu_tc", ctypes.c_int),
     ]
 
 

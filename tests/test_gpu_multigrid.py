@@ -283,3 +283,52 @@ def test_slab_solve_with_diagonal_vanka(precision, d, n, r, k, amp, nu, tau, pna
     Ud, _ = marching.newton_direct(L0.space, L0.td, U0, Vp, prob, 0.2, tol=1e-13)
     nv = (k + 1) * L0.lay.Nv
     assert _rel(_np(U)[:nv], Ud[:nv]) < 1e-7
+
+
+@pytest.mark.parametrize("d,n,r,k,amp,prec", [(2, 8, 2, 2, 0.15, "fp64"), (2, 6, 1, 1, 0.0, "fp32"),
+                                              (3, 3, 1, 1, 0.1, "fp64")])
+def test_exact_vanka_sweeps_match_oracle(d, n, r, k, amp, prec):
+    """Exact space-time patches (smoother = 2; the convection of each time node at its own velocity):
+    sweeps on every smoothed level against the oracle's ExactVanka (FP64 1e-9, FP32 2e-3)."""
+    import torch
+    from paper_2602_13841_gb300 import stmg
+    build_and_load()
+    verts = inputs.vertices(d, n, amp, 5)
+    p = stmg.default_params(dim=d, n_cells_1d=n, r=r, k=k, nu=0.01, tau=0.05, problem="TG2D" if d == 2 else "TG3D",
+                            precond_precision=stmg.STMG_FP64 if prec == "fp64" else stmg.STMG_FP32, smoother=2)
+    S = stmg.Solver(p, verts)
+    mg = multigrid.Multigrid(d, n, r, k, verts, 0.05, 0.01, smoother="exact")
+    dt = S.pdtype
+    tol = 1e-9 if prec == "fp64" else 2e-3
+    U = inputs.uniform(mg.levels[0].Nst, 7)
+    mg.setup(U)
+    S.smoother_build(_t(U))
+    for l in range(len(mg.levels) - 1):
+        L = mg.levels[l]
+        rhs = inputs.uniform(L.Nst, 30 + l)
+        d0 = inputs.uniform(L.Nst, 40 + l)
+        want = mg.smoothers[l].sweep(mg.J[l], rhs, d0)
+        got = _t(d0, dt)
+        S.smoother_sweep(l, _t(rhs, dt), got, 1, zero_start=False)
+        assert _rel(_np(got), want) < tol, l
+
+
+def test_slab_solve_with_exact_patches():
+    """The slab solve with exact patches reaches the Newton tolerance and the exact solution."""
+    import torch
+    d, n, r, k, nu, tau = 2, 8, 2, 2, 1e-3, 0.05
+    S, mg, verts = _setup(d, n, r, k, 0.1, precision="fp32", nu=nu, tau=tau, problem="TG2D",
+                          newton_rtol=1e-10, newton_atol=0.0, smoother=2)
+    L0 = mg.levels[0]
+    prob = problems.make("TG2D", nu)
+    V0 = torch.empty(L0.lay.Nv, dtype=torch.float64, device="cuda")
+    S.initial_condition(V0)
+    U = torch.empty(L0.Nst, dtype=torch.float64, device="cuda")
+    S.initial_guess(V0, U)
+    rc, st = S.slab_solve(0.2, V0, U)
+    assert rc == 0 and st["res_final"] <= 1e-10 * st["res0"]
+    Vp = _np(V0)
+    U0 = np.concatenate([np.tile(Vp, k + 1), np.zeros((k + 1) * L0.lay.Np)])
+    Ud, _ = marching.newton_direct(L0.space, L0.td, U0, Vp, prob, 0.2, tol=1e-13)
+    nv = (k + 1) * L0.lay.Nv
+    assert _rel(_np(U)[:nv], Ud[:nv]) < 1e-7

@@ -170,3 +170,30 @@ def test_diagonal_vanka_patch_is_the_spatially_diagonal_surrogate():
         want = np.linalg.solve(Sd, b)
         assert np.abs(sla.lu_solve(lu, b) - want).max() < 1e-11 * np.abs(want).max()
         assert np.abs(sla.lu_solve(lu_full, b) - want).max() > 1e-6 * np.abs(want).max()
+
+
+def test_exact_vanka_patches_are_submatrices_of_the_true_jacobian():
+    """ExactVanka uses R_K J R_K^T with the convection at each time node's own velocity (the
+    brute-force J of the first test), and differs from the surrogate when V depends on time."""
+    n, r, k, nu, tau = 2, 1, 1, 0.03, 0.2
+    that = np.array([-1.0 / 3.0, 1.0])
+    K = [[9 / 8, 3 / 8], [-9 / 8, 5 / 8]]
+    w = 0.5 * tau * np.array([1.5, 0.5])
+    X, Y = _nodes_xy(n, r)
+    f0, f1 = _affine(X, Y, F0), _affine(X, Y, F1)
+    Va = [np.concatenate([(f0 + t * f1)[:, 0], (f0 + t * f1)[:, 1]]) for t in that]
+    A0, B, Ms = _brute_force_operator(n, r, nu, Va[0], 10.0, 10.0, with_mass=True)
+    A1, _ = _brute_force_operator(n, r, nu, Va[1], 10.0, 10.0)
+    J = _slab_matrix(K, w, Ms, [A0, A1], B)
+    lvl = multigrid.Level(2, n, r, k, uniform_vertices(2, n), tau, nu)
+    U = np.zeros(lvl.Nst)
+    U[:2 * Ms.shape[0]] = np.concatenate(Va)
+    ex = multigrid.ExactVanka(lvl, U, 0.3, 1.0)
+    sur = multigrid.Vanka(lvl, U, 0.3, 1.0)
+    import scipy.linalg as sla
+    rng = np.random.default_rng(9)
+    for (idx, lu), (_, lus) in zip(ex.patches, sur.patches):
+        b = rng.uniform(-1, 1, len(idx))
+        want = np.linalg.solve(J[np.ix_(idx, idx)], b)
+        assert np.abs(sla.lu_solve(lu, b) - want).max() < 1e-11 * np.abs(want).max()
+        assert np.abs(sla.lu_solve(lus, b) - want).max() > 1e-8 * np.abs(want).max()
