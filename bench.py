@@ -155,9 +155,73 @@ def oracle_child(n, smooth, workload, smooth_tc=0):
     res = subprocess.run(cmd, capture_output=True, text=True, timeout=1800)
     if res.returncode != 0:
         return {"value": None, "unit": "DoF/s", "kind": "oracle", "error": res.stderr.strip()[-300:]}
-    v, desc = json.loads(res.stdout.strip().splitlines()[-1])
-    return {"value": v, "unit": "DoF/s", "cores": 1, "cpu_model": _cpu_model(), "host_cores": _host_cores(),
-            "kind": "oracle", "sample": desc}
+    v, desc, extra = json.loads(res.stdout.strip().splitlines()[-1])
+    out = {"value": v, "unit": "DoF/s", "cores": 1, "cpu_model": _cpu_model(), "host_cores": _host_cores(),
+           "kind": "oracle", "sample": desc}
+    out.update(extra)
+    return out
+
+
+def _replica(args):
+    """One oracle slab-solve sample in a worker process (all-cores replicas)."""
+    n, smooth, workload, smooth_tc = args
+    return oracle_sample(n=n, smooth=smooth, w=WORKLOADS[workload], smooth_tc=smooth_tc)[0]
+
+
+def oracle_breadth(workload, n, smooth, smooth_tc):
+    """Per-kernel oracle rates on the host (one BLAS thread): the operator apply (assembled Jacobian
+    times a vector, assembly included: the oracle's apply) on the C1 and C2 recipes and on 3D
+    sub-meshes of the C3 / C4 recipes, one Vanka sweep and one V-cycle on a C2 sub-mesh, and the
+    slab-solve sample replicated on every host core (independent processes)."""
+    import multiprocessing as mp
+    from oracle import forms, multigrid
+    from oracle.mesh import Mesh, Space
+    from oracle.reference import TimeData
+    from paper_2602_13841_gb300 import inputs
+    out = {}
+    cases = [("C1 2D 8^2 r=1 k=1", 2, 8, 1, 1, 0.0), ("C2 recipe 2D 32^2 r=2 k=2", 2, 32, 2, 2, 0.1),
+             ("C3 recipe 3D 3^3 r=2 k=1", 3, 3, 2, 1, 0.0), ("C4 recipe 3D 4^3 r=1 k=2", 3, 4, 1, 2, 0.1)]
+    app = {}
+    for name, d, nn, r, k, amp in cases:
+        sp = Space(Mesh(d, nn, inputs.vertices(d, nn, amp, 1234)), r)
+        td = TimeData(k, 0.05)
+        lay = forms.SlabLayout(sp, k)
+        U = inputs.uniform(lay.Nst, 43)
+        x = inputs.uniform(lay.Nst, 42)
+        t = time.perf_counter()
+        forms.apply(sp, td, U, x, 1e-3)
+        dt = time.perf_counter() - t
+        app[name] = {"n_st": lay.Nst, "dof_per_s": lay.Nst / dt, "seconds": dt}
+    out["apply"] = app
+    # smoother sweep and V-cycle on the C2 recipe at 16^2 (the workload's smoothing counts)
+    w = WORKLOADS["2d"]
+    mg = multigrid.Multigrid(2, 16, w["r"], w["k"], inputs.vertices(2, 16, w["amp"], w["seed"]), w["tau"], w["nu"],
+                             nu1=smooth, nu2=smooth, nu_tc=smooth_tc)
+    L0 = mg.levels[0]
+    U = inputs.uniform(L0.Nst, 7)
+    t = time.perf_counter()
+    mg.setup(U)
+    t_setup = time.perf_counter() - t
+    rhs = inputs.uniform(L0.Nst, 8)
+    t = time.perf_counter()
+    mg.smoothers[0].sweep(mg.J[0], rhs, np.zeros(L0.Nst))
+    t_sweep = time.perf_counter() - t
+    t = time.perf_counter()
+    mg.vcycle(rhs)
+    t_vc = time.perf_counter() - t
+    out["multigrid_c2_recipe_16sq"] = {"n_st": L0.Nst, "setup_s": t_setup, "sweep_s": t_sweep, "vcycle_s": t_vc}
+    # all host cores: the slab-solve sample as independent replicas, one per core
+    cores = _host_cores()
+    ctx = mp.get_context("spawn")
+    t = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        pool.map(_replica, [(n, smooth, workload, smooth_tc)] * cores)
+    dt = time.perf_counter() - t
+    nst = oracle_sample(n=n, smooth=smooth, w=WORKLOADS[workload], smooth_tc=smooth_tc)[2]
+    out["all_cores"] = {"cores": cores, "value": cores * nst / dt, "unit": "DoF/s",
+                        "sample": "%d replicas of the slab-solve sample in %d processes (spawned), wall %.1f s" %
+                                  (cores, cores, dt)}
+    return out
 
 
 def _host_cores():
@@ -245,15 +309,18 @@ def main():
                     help="slabs timed with the plain FP64 preconditioner beside the headline (0: skip)")
     ap.add_argument("--variant-smooth", type=int, default=2,
                     help="sweeps of the space-only p-coarsening variant timed beside the headline (0: skip)")
-    ap.add_argument("--serving-requests", type=int, default=16,
+    ap.add_argument("--serving-requests", type=int, default=200,
                     help="requests of the serving leg (Poisson stream, 20/s); 0 skips it")
     ap.add_argument("--oracle-child", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     W = WORKLOADS[args.workload]
     if args.oracle_child:
-        v, dt, nst, desc = oracle_sample(n=args.ref_n or W["oracle_n"], smooth=args.smooth or W["smooth"], w=W,
-                                         smooth_tc=args.smooth_tc if args.smooth_tc >= 0 else W.get("smooth_tc", 0))
-        print(json.dumps([v, desc]), flush=True)
+        n = args.ref_n or W["oracle_n"]
+        sm = args.smooth or W["smooth"]
+        tc = args.smooth_tc if args.smooth_tc >= 0 else W.get("smooth_tc", 0)
+        v, dt, nst, desc = oracle_sample(n=n, smooth=sm, w=W, smooth_tc=tc)
+        extra = oracle_breadth(args.workload, n, sm, tc) if args.workload == "2d" else {}
+        print(json.dumps([v, desc, extra]), flush=True)
         return
     if args.n <= 0:
         args.n = W["n"]
@@ -446,22 +513,28 @@ def main():
     serving = None
     if args.serving_requests > 0:
         from paper_2602_13841_gb300 import serving as srv
-        # the serving workload's distribution restricted to what the smoother supports in 3D
-        # (r <= 2; Q3/P2 patches, factorised in global memory, only up to 8^3 cells to bound the
-        # request time); seeded Poisson arrivals at 20 requests per second
+        # the serving workload's distribution; 3D Q3/P2 and Q4/P3 patches (factorised in global
+        # memory, the build dominating the request time) only up to 8^3 cells to bound the request
+        # time; seeded Poisson arrivals at 20 requests per second
         reqs = srv.poisson_stream(args.serving_requests, 20.0, 7, orders=(1, 2, 3), ks=(0, 1, 2))
         for q in reqs:
-            if q.d == 3:
-                q.r = min(q.r, 2)
-                if q.r == 2:
-                    q.n = min(q.n, 8)
+            if q.d == 3 and q.r >= 2:
+                q.n = min(q.n, 8)
         server = srv.Server(workers=4)
+        l0 = lib.stmg_launch_count()
         res = server.run(reqs, realtime=True)
         server.close()
         serving = srv.report(res)
         serving["workers"] = 4
+        serving["kernel_launches"] = int(lib.stmg_launch_count() - l0)
+        bs = server.batch_stats()
+        if bs["rounds"]:
+            # the per-request path launches the same chain once per slot V-cycle
+            per_round = bs["launches"] / bs["rounds"]
+            bs["launches_saved"] = int(round(per_round * bs["slot_vcycles"] - bs["launches"]))
+        serving["batching"] = bs
         serving["stream"] = ("Poisson 20/s seed 7; 2D n in {16..256}, 3D n in {8..48}, r in {1,2,3} "
-                             "(3D r<=2, 3D r=2 with n<=8), k in {0,1,2}, Re ~ U[100,2000]; one slab each")
+                             "(3D r>=2 with n<=8), k in {0,1,2}, Re ~ U[100,2000]; one slab each")
 
     if rank == 0:
         cpu = None

@@ -280,6 +280,39 @@ long long stmg_launch_count(void);
 stmg_status stmg_slab_solve(stmg_handle* h, double t_start, const double* V_prev, double* U,
                             stmg_stats* stats);
 
+/* ---- Batched preconditioning across same-shape solves (continuous batching of requests) ----
+ * A group holds one hp-STMG hierarchy with `slots` slots for handles of one shape (the same
+ * stmg_params except viscosity and problem data, the same vertices).  An attached handle's
+ * smoother builds fill its own slot, and each preconditioner application (one per FGMRES
+ * iteration) joins the next batched V-cycle of the group: every kernel of the V-cycle chain
+ * (level residuals, Vanka sweeps, transfers, coarse solve) is launched once for all ready slots.
+ * Batching is the serving pattern of concurrent same-shape requests; the paper has no
+ * counterpart (its solver runs one problem at a time).  A round starts as soon as every attached
+ * handle that is inside stmg_slab_solve is waiting, or 200 microseconds after the first one
+ * arrived.  Each slot computes exactly what a handle without a group computes, so results are
+ * bitwise the same alone and in a batch.  Slab solves of attached handles must run on different
+ * host threads (they wait for each other); stmg_smoother_sweep / stmg_vcycle / stmg_transfer /
+ * stmg_level_state are not available on attached handles (STMG_ERR_ARG).  The group runs on its
+ * own stream (`stream`), ordered against the handles' streams by events.  Device memory: the
+ * hierarchy of `slots` handles (an attached handle allocates no hierarchy of its own). */
+typedef struct stmg_group stmg_group;
+
+/* Create a group for handles shaped like p / vertices (as stmg_create), 1 <= slots <= 16. */
+stmg_status stmg_group_create(const stmg_params* p, const double* vertices, int slots, stmg_stream stream,
+                              stmg_group** out);
+/* Destroy a group; attached handles are detached first (their next solve allocates their own
+ * hierarchy).  No solve of an attached handle may be running. */
+void stmg_group_destroy(stmg_group* g);
+/* Attach a handle to a free slot; STMG_ERR_ARG if the shape differs or no slot is free.  Attach
+ * before the handle's first smoother build or slab solve. */
+stmg_status stmg_group_attach(stmg_group* g, stmg_handle* h);
+stmg_status stmg_group_detach(stmg_group* g, stmg_handle* h);
+/* Counters: batched V-cycle rounds, slot V-cycles served (the V-cycles the handles asked for),
+ * kernel launches of the rounds' V-cycles (the per-handle path would launch about
+ * launches / rounds * slot_vcycles). */
+stmg_status stmg_group_stats(const stmg_group* g, long long* rounds, long long* slot_vcycles,
+                             long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

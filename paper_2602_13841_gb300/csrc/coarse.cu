@@ -167,6 +167,9 @@ cudaError_t coarse_invert(const double* A, double* Ainv, double* col, int* piv, 
 
 template <typename TA>
 __global__ void k_gemv_cm(const TA* __restrict__ A, int n, const double* __restrict__ x, double* __restrict__ y) {
+  A += (int64_t)blockIdx.y * n * n;           // blockIdx.y: independent slot
+  x += (int64_t)blockIdx.y * n;
+  y += (int64_t)blockIdx.y * n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double acc = 0.0;
     for (int j = 0; j < n; ++j) acc += (double)A[(int64_t)j * n + i] * x[j];
@@ -174,8 +177,8 @@ __global__ void k_gemv_cm(const TA* __restrict__ A, int n, const double* __restr
   }
 }
 
-cudaError_t gemv_cm(const double* A, int n, const double* x, double* y, cudaStream_t s) {
-  k_gemv_cm<double><<<(n + 127) / 128, 128, 0, s>>>(A, n, x, y);
+cudaError_t gemv_cm(const double* A, int n, const double* x, double* y, cudaStream_t s, int slots) {
+  k_gemv_cm<double><<<dim3((n + 127) / 128, slots), 128, 0, s>>>(A, n, x, y);
   note_launch();
   return cudaGetLastError();
 }

@@ -64,6 +64,9 @@ struct Handle {
   bool user_valid = false;
   std::vector<double> verts0;         // host copy of the finest level's vertices
   bool solver_ready = false;
+  // batched preconditioning: the group this handle is attached to and its slot there
+  struct Group* group = nullptr;
+  int slot = -1;
   bool timing = false;
   bool wait_fault = false;           // failure-test hook: Vanka applies wait for bytes never sent
   PhaseTimer t_rebuild, t_mg;

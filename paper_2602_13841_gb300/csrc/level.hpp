@@ -53,9 +53,11 @@ cudaError_t launch_operator(const Level& lv, const Problem& pb, int mode, double
 
 // y = rhs - J(state) x on a level (rhs null: y = J(state) x), the residual of a multigrid sweep;
 // one launch where the tiled 2D kernel applies, else the operator followed by a vector update.
+// `columns` independent residuals at strides n_st (own rhs, x, state, y; per-column viscosity
+// nub[column] on the device, or null for pb.nu).
 template <typename T>
 cudaError_t launch_level_residual(const Level& lv, const Problem& pb, const T* rhs, const T* x, const T* state, T* y,
-                                  cudaStream_t stream);
+                                  cudaStream_t stream, int columns = 1, const T* nub = nullptr);
 
 cudaError_t launch_initial_condition(const Level& lv, const Problem& pb, double* V0, cudaStream_t s);
 

@@ -12,28 +12,34 @@ namespace stmg {
 #define CKE(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return e_; } while (0)
 
 template <typename T>
-cudaError_t MG<T>::allocate(Handle* hh) {
+cudaError_t MG<T>::allocate(Handle* hh, int slots) {
   h = hh;
+  B = slots < 1 ? 1 : slots;
   nl = (int)h->levels.size();
   U.resize(nl); r.resize(nl); z.resize(nl); t.resize(nl); q.resize(nl); inv.assign(nl, nullptr);
   invh.assign(nl, nullptr); iscale.assign(nl, nullptr);
+  inv_slot.assign(nl, 0); invh_slot.assign(nl, 0); scale_slot.assign(nl, 0);
   size_t ea = 0, eb = 0, em = 0, nv = 0, wk = 0;
   try {
+    if (B > 1) nub = (T*)h->dalloc(B * sizeof(T));
     for (int l = 0; l < nl; ++l) {
       const Level& lv = h->levels[l];
-      U[l] = (T*)h->dalloc(lv.Nst * sizeof(T));
-      r[l] = (T*)h->dalloc(lv.Nst * sizeof(T));
-      z[l] = (T*)h->dalloc(lv.Nst * sizeof(T));
-      t[l] = (T*)h->dalloc(lv.Nst * sizeof(T));
-      q[l] = (T*)h->dalloc(lv.Nst * sizeof(T));
+      U[l] = (T*)h->dalloc(B * lv.Nst * sizeof(T));
+      r[l] = (T*)h->dalloc(B * lv.Nst * sizeof(T));
+      z[l] = (T*)h->dalloc(B * lv.Nst * sizeof(T));
+      t[l] = (T*)h->dalloc(B * lv.Nst * sizeof(T));
+      q[l] = (T*)h->dalloc(B * lv.Nst * sizeof(T));
       if (l < nl - 1) {
         if (!vanka_supported(lv, sizeof(T))) { smoothable = false; continue; }
-        size_t m = vanka_patch_size(lv);
+        const int64_t cells = lv.Np / lv.npc;
         if (h->prm.vanka_fp16 && lv.smoother == 0) {
-          invh[l] = h->dalloc((size_t)(lv.Np / lv.npc) * vanka_inv_entries(lv, 2) * 2);
-          iscale[l] = (float*)h->dalloc((size_t)(lv.Np / lv.npc) * (lv.k + 1) * sizeof(float));
+          invh_slot[l] = cells * (int64_t)vanka_inv_entries(lv, 2);
+          scale_slot[l] = cells * (lv.k + 1);
+          invh[l] = h->dalloc((size_t)B * invh_slot[l] * 2);
+          iscale[l] = (float*)h->dalloc((size_t)B * scale_slot[l] * sizeof(float));
         } else {
-          inv[l] = (T*)h->dalloc((size_t)(lv.Np / lv.npc) * vanka_inv_entries(lv, (int)sizeof(T)) * sizeof(T));
+          inv_slot[l] = cells * (int64_t)vanka_inv_entries(lv, (int)sizeof(T));
+          inv[l] = (T*)h->dalloc((size_t)B * inv_slot[l] * sizeof(T));
         }
         size_t nc = lv.Np / lv.npc;
         const size_t ec = vanka_elem_cells(lv);                 // element scratch: one chunk
@@ -54,18 +60,18 @@ cudaError_t MG<T>::allocate(Handle* hh) {
     status = (int*)h->dalloc(sizeof(int));
     wstat = (int*)h->dalloc(sizeof(int));
     tr.resize(nl > 0 ? nl - 1 : 0);
-    for (int l = 0; l + 1 < nl; ++l) build_transfer(h, tr[l], h->levels[l], h->levels[l + 1], sizeof(T));
+    for (int l = 0; l + 1 < nl; ++l) build_transfer(h, tr[l], h->levels[l], h->levels[l + 1], sizeof(T), B);
     const Level& c = h->levels[nl - 1];
     Nc = (int)c.Nst;
     Nb = Nc + c.k + 1;
-    A64 = (double*)h->dalloc((size_t)Nb * Nb * sizeof(double));
+    A64 = (double*)h->dalloc((size_t)B * Nb * Nb * sizeof(double));
     ident = (double*)h->dalloc(((size_t)Nc * Nc + 2 * (size_t)Nc) * sizeof(double));
     Ucs = (double*)h->dalloc((size_t)Nc * sizeof(double));
-    cb = (double*)h->dalloc((size_t)Nb * sizeof(double));
-    cx = (double*)h->dalloc((size_t)Nb * sizeof(double));
-    cr = (double*)h->dalloc((size_t)Nb * sizeof(double));
-    cw = (double*)h->dalloc((size_t)Nb * sizeof(double));
-    Ainv = (double*)h->dalloc((size_t)Nb * Nb * sizeof(double));
+    cb = (double*)h->dalloc((size_t)B * Nb * sizeof(double));
+    cx = (double*)h->dalloc((size_t)B * Nb * sizeof(double));
+    cr = (double*)h->dalloc((size_t)B * Nb * sizeof(double));
+    cw = (double*)h->dalloc((size_t)B * Nb * sizeof(double));
+    Ainv = (double*)h->dalloc((size_t)B * Nb * Nb * sizeof(double));
     gj_col = (double*)h->dalloc((size_t)Nb * sizeof(double));
     gj_piv = (int*)h->dalloc((size_t)Nb * sizeof(int));
   } catch (const std::bad_alloc&) {
@@ -92,33 +98,44 @@ cudaError_t MG<T>::check_wait() {
 }
 
 template <typename T>
-cudaError_t MG<T>::setup(const double* U64) {
+cudaError_t MG<T>::setup(const double* U64, int slot, const Problem* pbp) {
   cudaStream_t s = h->stream;
   const Level& f = h->levels[0];
+  const Problem& pb = pbp ? *pbp : h->pb;
   if (!smoothable) return cudaErrorNotSupported;
+  if (slot < 0 || slot >= B) return cudaErrorInvalidValue;
   CKE(cudaMemsetAsync(status, 0, sizeof(int), s));
   CKE(cudaMemsetAsync(wstat, 0, sizeof(int), s));
-  CKE((vcopy<double, T>(f.Nst, U64, U[0], s)));
+  if (nub) {
+    const T nuv = (T)pb.nu;
+    CKE(cudaMemcpyAsync(nub + slot, &nuv, sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+  auto lvec = [&](std::vector<T*>& v, int l) { return v[l] + (int64_t)slot * h->levels[l].Nst; };
+  CKE((vcopy<double, T>(f.Nst, U64, lvec(U, 0), s)));
   for (int l = 0; l + 1 < nl; ++l) {
     const Level& c = h->levels[l + 1];
-    CKE(cudaMemsetAsync(U[l + 1], 0, c.Nst * sizeof(T), s));
-    CKE(tr[l].template interp_state<T>(U[l], U[l + 1], s));
+    CKE(cudaMemsetAsync(lvec(U, l + 1), 0, c.Nst * sizeof(T), s));
+    CKE(tr[l].template interp_state<T>(lvec(U, l), lvec(U, l + 1), s));
   }
   for (int l = 0; l + 1 < nl; ++l) {
     h->kbegin(KC_VANKA_BUILD);
-    CKE(vanka_build<T>(h->levels[l], h->pb, U[l], vstar, EA, EB, EM, inv[l], invh[l], iscale[l], status, work, s));
+    CKE(vanka_build<T>(h->levels[l], pb, lvec(U, l), vstar, EA, EB, EM,
+                       inv[l] ? inv[l] + slot * inv_slot[l] : nullptr,
+                       invh[l] ? (void*)((unsigned short*)invh[l] + slot * invh_slot[l]) : nullptr,
+                       iscale[l] ? iscale[l] + slot * scale_slot[l] : nullptr, status, work, s));
     h->kend(KC_VANKA_BUILD, 0.0, 4);
   }
   // coarse: assemble J_c at the coarse state by a batched apply to the identity
   const Level& c = h->levels[nl - 1];
-  CKE((vcopy<T, double>(c.Nst, U[nl - 1], Ucs, s)));
+  double* A64s = A64 + (int64_t)slot * Nb * Nb;
+  CKE((vcopy<T, double>(c.Nst, lvec(U, nl - 1), Ucs, s)));
   k_identity<<<152 * 4, 256, 0, s>>>(ident, Nc);
   note_launch();
-  CKE(launch_operator<double>(c, h->pb, OP_JAC, 0.0, ident, Ucs, nullptr, A64, s, Nc, Nc, Nc));
+  CKE(launch_operator<double>(c, pb, OP_JAC, 0.0, ident, Ucs, nullptr, A64s, s, Nc, Nc, Nc));
   // A64 now holds J (N x N, column-major); move into the bordered layout via `ident` as staging
-  CKE(cudaMemcpyAsync(ident, A64, (size_t)Nc * Nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  CKE(coarse_border(c, h->pb, ident, A64, Nc, Nb, s));
-  CKE(coarse_invert(A64, Ainv, gj_col, gj_piv, Nb, status, s));
+  CKE(cudaMemcpyAsync(ident, A64s, (size_t)Nc * Nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CKE(coarse_border(c, pb, ident, A64s, Nc, Nb, s));
+  CKE(coarse_invert(A64s, Ainv + (int64_t)slot * Nb * Nb, gj_col, gj_piv, Nb, status, s));
   int st = 0;
   CKE(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CKE(cudaStreamSynchronize(s));
@@ -127,35 +144,35 @@ cudaError_t MG<T>::setup(const double* U64) {
 }
 
 template <typename T>
-cudaError_t MG<T>::coarse_solve(const T* rhs, T* d) {
+cudaError_t MG<T>::coarse_solve(const T* rhs, T* d, int slots) {
   cudaStream_t s = h->stream;
-  CKE(cudaMemsetAsync(cb, 0, Nb * sizeof(double), s));
-  CKE((vcopy<T, double>(Nc, rhs, cb, s)));
-  CKE(gemv_cm(Ainv, Nb, cb, cx, s));
+  CKE(cudaMemsetAsync(cb, 0, (size_t)slots * Nb * sizeof(double), s));
+  CKE((vcopy_slots<T, double>(Nc, slots, rhs, Nc, cb, Nb, s)));
+  CKE(gemv_cm(Ainv, Nb, cb, cx, s, slots));
   for (int it = 0; it < 1; ++it) {          // one step of iterative refinement
-    CKE(gemv_cm(A64, Nb, cx, cw, s));
-    CKE(cudaMemcpyAsync(cr, cb, Nb * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CKE(vaxpby<double>(Nb, -1.0, cw, 1.0, cr, s));
-    CKE(gemv_cm(Ainv, Nb, cr, cw, s));
-    CKE(vaxpby<double>(Nb, 1.0, cw, 1.0, cx, s));
+    CKE(gemv_cm(A64, Nb, cx, cw, s, slots));
+    CKE(cudaMemcpyAsync(cr, cb, (size_t)slots * Nb * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CKE(vaxpby<double>((int64_t)slots * Nb, -1.0, cw, 1.0, cr, s));
+    CKE(gemv_cm(Ainv, Nb, cr, cw, s, slots));
+    CKE(vaxpby<double>((int64_t)slots * Nb, 1.0, cw, 1.0, cx, s));
   }
-  CKE((vcopy<double, T>(Nc, cx, d, s)));
+  CKE((vcopy_slots<double, T>(Nc, slots, cx, Nb, d, Nc, s)));
   return cudaSuccess;
 }
 
 template <typename T>
-cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start) {
+cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start, int slots) {
   cudaStream_t s = h->stream;
   const Level& lv = h->levels[l];
   const double omega = h->prm.omega;
   for (int it = 0; it < nsweeps; ++it) {
     const T* res = rhs;
     if (it == 0 && zero_start) {
-      CKE(cudaMemsetAsync(d, 0, lv.Nst * sizeof(T), s));
+      CKE(cudaMemsetAsync(d, 0, (size_t)slots * lv.Nst * sizeof(T), s));
     } else {
       // q = rhs - J d
       h->kbegin(KC_APPLYP);
-      CKE(launch_level_residual<T>(lv, h->pb, rhs, d, U[l], q[l], s));
+      CKE(launch_level_residual<T>(lv, h->pb, rhs, d, U[l], q[l], s, slots, slots > 1 ? nub : nullptr));
       h->kend(KC_APPLYP);
       res = q[l];
     }
@@ -171,8 +188,8 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
     if (l == 0) h->kbegin(KC_VANKA_APPLY0);
     for (int c = 0; c < lv.ncolors; ++c) {
       CKE(vanka_apply<T>(lv, h->pb, inv[l], invh[l], iscale[l], res, d, omega, h->prm.omega_p, c, wstat, s,
-                         h->wait_fault ? 16u : 0u));
-      cells += lv.colors[c].count;
+                         h->wait_fault ? 16u : 0u, slots));
+      cells += (int64_t)slots * lv.colors[c].count;
     }
     if (l == 0) h->kend(KC_VANKA_APPLY0, (double)cells * (ib + 3.0 * m * sizeof(T)), lv.ncolors);
     h->kend(KC_VANKA_APPLY, (double)cells * (ib + 3.0 * m * sizeof(T)), lv.ncolors);
@@ -181,30 +198,30 @@ cudaError_t MG<T>::sweep(int l, const T* rhs, T* d, int nsweeps, bool zero_start
 }
 
 template <typename T>
-cudaError_t MG<T>::vcycle_level(int l, const T* rhs, T* d) {
-  if (l == nl - 1) return coarse_solve(rhs, d);
+cudaError_t MG<T>::vcycle_level(int l, const T* rhs, T* d, int slots) {
+  if (l == nl - 1) return coarse_solve(rhs, d, slots);
   cudaStream_t s = h->stream;
   const Level& lv = h->levels[l];
   int nu1 = h->prm.nu1 > 0 ? h->prm.nu1 : 0, nu2 = h->prm.nu2 > 0 ? h->prm.nu2 : 0;
   // levels whose next coarser level has a lower time degree: nu_tc sweeps each way when set
   if (h->prm.nu_tc > 0 && h->levels[l + 1].k < lv.k) nu1 = nu2 = h->prm.nu_tc;
-  if (nu1 > 0) CKE(sweep(l, rhs, d, nu1, true));
-  else CKE(cudaMemsetAsync(d, 0, lv.Nst * sizeof(T), s));
+  if (nu1 > 0) CKE(sweep(l, rhs, d, nu1, true, slots));
+  else CKE(cudaMemsetAsync(d, 0, (size_t)slots * lv.Nst * sizeof(T), s));
   // t = rhs - J d ; r_{l+1} = P^T t
   h->kbegin(KC_APPLYP);
-  CKE(launch_level_residual<T>(lv, h->pb, rhs, d, U[l], t[l], s));
+  CKE(launch_level_residual<T>(lv, h->pb, rhs, d, U[l], t[l], s, slots, slots > 1 ? nub : nullptr));
   h->kend(KC_APPLYP);
-  CKE(tr[l].template restrict_<T>(t[l], r[l + 1], s));
-  CKE(vcycle_level(l + 1, r[l + 1], z[l + 1]));
-  CKE(tr[l].template prolong<T>(z[l + 1], t[l], s));
-  CKE(vaxpby<T>(lv.Nst, (T)1, t[l], (T)1, d, s));
-  if (nu2 > 0) CKE(sweep(l, rhs, d, nu2, false));
+  CKE(tr[l].template restrict_<T>(t[l], r[l + 1], s, slots));
+  CKE(vcycle_level(l + 1, r[l + 1], z[l + 1], slots));
+  CKE(tr[l].template prolong<T>(z[l + 1], t[l], s, slots));
+  CKE(vaxpby<T>((int64_t)slots * lv.Nst, (T)1, t[l], (T)1, d, s));
+  if (nu2 > 0) CKE(sweep(l, rhs, d, nu2, false, slots));
   return cudaSuccess;
 }
 
 template <typename T>
-cudaError_t MG<T>::vcycle(const T* rhs, T* zz) {
-  return vcycle_level(0, rhs, zz);
+cudaError_t MG<T>::vcycle(const T* rhs, T* zz, int slots) {
+  return vcycle_level(0, rhs, zz, slots > 0 ? slots : B);
 }
 
 template <typename T>
@@ -218,9 +235,9 @@ void MG<T>::drop_graph() {
 }
 
 template <typename T>
-cudaError_t MG<T>::vcycle_graph() {
+cudaError_t MG<T>::vcycle_graph(int slots) {
   cudaStream_t s = h->stream;
-  if (graph_exec && (graph_timing != h->timing || graph_kmask != h->kmask)) drop_graph();
+  if (graph_exec && (graph_timing != h->timing || graph_kmask != h->kmask || graph_slots != slots)) drop_graph();
   if (!graph_exec) {
     // capture the V-cycle on r[0] -> z[0]; all buffers and parameters are fixed per handle, so
     // the graph stays valid across smoother rebuilds
@@ -229,7 +246,7 @@ cudaError_t MG<T>::vcycle_graph() {
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) { h->capsink = nullptr; return e; }
     const long long n0 = launch_count();
-    cudaError_t ev = vcycle_level(0, r[0], z[0]);
+    cudaError_t ev = vcycle_level(0, r[0], z[0], slots);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s, &g);
     h->capsink = nullptr;
@@ -242,6 +259,7 @@ cudaError_t MG<T>::vcycle_graph() {
     CKE(cudaGraphInstantiate(&graph_exec, graph, 0));
     graph_timing = h->timing;
     graph_kmask = h->kmask;
+    graph_slots = slots;
   }
   CKE(cudaGraphLaunch(graph_exec, s));
   note_launch(graph_kernels);

@@ -19,11 +19,11 @@ cudaError_t launch_operator<float>(const Level& lv, const Problem& pb, int mode,
 
 template <>
 cudaError_t launch_level_residual<float>(const Level& lv, const Problem& pb, const float* rhs, const float* x,
-                                         const float* state, float* y, cudaStream_t s) {
-  cudaError_t e = launch_jac_tiled<float>(lv, pb, x, state, rhs, y, s);
+                                       const float* state, float* y, cudaStream_t s, int columns, const float* nub) {
+  cudaError_t e = launch_jac_tiled<float>(lv, pb, x, state, rhs, y, s, columns, nub);
   if (e != cudaErrorNotSupported) return e;
-  e = launch_any<float, MJ>(lv, pb, 0.0, x, state, nullptr, y, s, 1, 0, 0);
-  if (e == cudaSuccess && rhs) e = vaxpby<float>(lv.Nst, 1.0f, rhs, -1.0f, y, s);
+  e = launch_any<float, MJ>(lv, pb, 0.0, x, state, nullptr, y, s, columns, lv.Nst, lv.Nst, lv.Nst, nub);
+  if (e == cudaSuccess && rhs) e = vaxpby<float>(columns * lv.Nst, 1.0f, rhs, -1.0f, y, s);
   return e;
 }
 

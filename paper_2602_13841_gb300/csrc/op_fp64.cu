@@ -17,11 +17,11 @@ cudaError_t launch_operator<double>(const Level& lv, const Problem& pb, int mode
 
 template <>
 cudaError_t launch_level_residual<double>(const Level& lv, const Problem& pb, const double* rhs, const double* x,
-                                          const double* state, double* y, cudaStream_t s) {
-  cudaError_t e = launch_jac_tiled<double>(lv, pb, x, state, rhs, y, s);
+                                       const double* state, double* y, cudaStream_t s, int columns, const double* nub) {
+  cudaError_t e = launch_jac_tiled<double>(lv, pb, x, state, rhs, y, s, columns, nub);
   if (e != cudaErrorNotSupported) return e;
-  e = launch_any<double, MJ>(lv, pb, 0.0, x, state, nullptr, y, s, 1, 0, 0);
-  if (e == cudaSuccess && rhs) e = vaxpby<double>(lv.Nst, 1.0, rhs, -1.0, y, s);
+  e = launch_any<double, MJ>(lv, pb, 0.0, x, state, nullptr, y, s, columns, lv.Nst, lv.Nst, lv.Nst, nub);
+  if (e == cudaSuccess && rhs) e = vaxpby<double>(columns * lv.Nst, 1.0, rhs, -1.0, y, s);
   return e;
 }
 

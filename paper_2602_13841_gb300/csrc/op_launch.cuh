@@ -41,7 +41,7 @@ static int face_smem_per_cell(int kp1) {
 template <typename T, int D, int N, int MODE>
 static cudaError_t launch_dn(const Level& lv, const Problem& pb, double t0, const T* x,
                              const T* state, const T* vprev, T* y, cudaStream_t stream,
-                             int batch, int64_t xs, int64_t ys) {
+                             int batch, int64_t xs, int64_t ys, int64_t ss = 0, const T* nub = nullptr) {
   constexpr int Q = Shape<D, N>::Q;
   const int kp1 = lv.k + 1;
   Tab<T> tb = make_tab<T>(lv.tabs, pb.tau);
@@ -49,7 +49,7 @@ static cudaError_t launch_dn(const Level& lv, const Problem& pb, double t0, cons
   if constexpr (D == 2) {
     if constexpr (std::is_same<T, double>::value) geo = lv.geo64; else geo = lv.geo32;
   }
-  OpArgs<T> A{level_args<T>(lv, pb, t0), x, state, vprev, y, xs, ys, geo};
+  OpArgs<T> A{level_args<T>(lv, pb, t0), x, state, vprev, y, xs, ys, geo, ss, nub};
   int cpb = 256 / Q; if (cpb < 1) cpb = 1;
   int smem = cpb * vol_smem_per_cell<T, D, N, MODE>(kp1);
   while (smem > 160 * 1024 && cpb > 1) { --cpb; smem = cpb * vol_smem_per_cell<T, D, N, MODE>(kp1); }
@@ -106,29 +106,30 @@ inline bool apply2d_tiled() {
 
 template <typename T, int N>
 static cudaError_t jac_tiled_n(const Level& lv, const Problem& pb, const T* x, const T* state, const T* rhs, T* y,
-                               cudaStream_t s) {
-  OpArgs<T> A{level_args<T>(lv, pb, 0.0), x, state, nullptr, y, 0, 0, nullptr};
+                               cudaStream_t s, int columns, const T* nub) {
+  OpArgs<T> A{level_args<T>(lv, pb, 0.0), x, state, nullptr, y, lv.Nst, lv.Nst, nullptr, lv.Nst, nub};
   const Tab<T> tb = make_tab<T>(lv.tabs, pb.tau);
   cudaError_t e = cudaErrorNotSupported;
-  if (lv.k == 0) e = launch_apply2d_tile<T, N, 1>(A, tb, rhs, lv.n, s);
-  else if (lv.k == 1) e = launch_apply2d_tile<T, N, 2>(A, tb, rhs, lv.n, s);
-  else if (lv.k == 2) e = launch_apply2d_tile<T, N, 3>(A, tb, rhs, lv.n, s);
+  if (lv.k == 0) e = launch_apply2d_tile<T, N, 1>(A, tb, rhs, lv.n, s, columns);
+  else if (lv.k == 1) e = launch_apply2d_tile<T, N, 2>(A, tb, rhs, lv.n, s, columns);
+  else if (lv.k == 2) e = launch_apply2d_tile<T, N, 3>(A, tb, rhs, lv.n, s, columns);
   if (e == cudaSuccess) note_launch();
   return e;
 }
 
 // y = J(state) x, or y = rhs - J(state) x when rhs is not null, by the tiled 2D kernel (one
-// launch, y written without a zero fill).  cudaErrorNotSupported where it does not apply (3D,
-// Q4/P3, FP64, or the colour kernels chosen).
+// launch, y written without a zero fill).  `columns` independent applies at strides n_st (own
+// increment, state, output and, with nub, viscosity).  cudaErrorNotSupported where it does not
+// apply (3D, Q4/P3, FP64, or the colour kernels chosen).
 template <typename T>
 cudaError_t launch_jac_tiled(const Level& lv, const Problem& pb, const T* x, const T* state, const T* rhs, T* y,
-                             cudaStream_t s) {
+                             cudaStream_t s, int columns = 1, const T* nub = nullptr) {
   if constexpr (!std::is_same<T, float>::value) {
     return cudaErrorNotSupported;
   } else {
     if (lv.d != 2 || !apply2d_tiled()) return cudaErrorNotSupported;
-    if (lv.r == 1) return jac_tiled_n<T, 3>(lv, pb, x, state, rhs, y, s);
-    if (lv.r == 2) return jac_tiled_n<T, 4>(lv, pb, x, state, rhs, y, s);
+    if (lv.r == 1) return jac_tiled_n<T, 3>(lv, pb, x, state, rhs, y, s, columns, nub);
+    if (lv.r == 2) return jac_tiled_n<T, 4>(lv, pb, x, state, rhs, y, s, columns, nub);
     return cudaErrorNotSupported;
   }
 }
@@ -136,9 +137,9 @@ cudaError_t launch_jac_tiled(const Level& lv, const Problem& pb, const T* x, con
 template <typename T, int MODE>
 static cudaError_t launch_any(const Level& lv, const Problem& pb, double t0, const T* x,
                               const T* state, const T* vprev, T* y, cudaStream_t s,
-                              int batch, int64_t xs, int64_t ys) {
+                              int batch, int64_t xs, int64_t ys, int64_t ss = 0, const T* nub = nullptr) {
   const int N = lv.r + 2;
-#define STMG_LAUNCH(DD, NN) return launch_dn<T, DD, NN, MODE>(lv, pb, t0, x, state, vprev, y, s, batch, xs, ys)
+#define STMG_LAUNCH(DD, NN) return launch_dn<T, DD, NN, MODE>(lv, pb, t0, x, state, vprev, y, s, batch, xs, ys, ss, nub)
   if (lv.d == 2) {
     if (N == 3) STMG_LAUNCH(2, 3);
     if (N == 4) STMG_LAUNCH(2, 4);

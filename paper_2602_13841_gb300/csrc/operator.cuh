@@ -71,7 +71,13 @@ struct OpArgs {
   int64_t xs, ys;    // batch strides (blockIdx.y selects the column of a batched apply)
   const T* geo;      // 2D: per cell [5][Q] inverse Jacobian G[0][0], G[0][1], G[1][0], G[1][1] and
                      // JxW at the quadrature points (precomputed at set-up), or null
+  int64_t ss;        // batch stride of the state (0: one state shared by the batch)
+  const T* nub;      // per-batch-column viscosity (device, blockIdx.y), or null: L.nu
 };
+
+// Viscosity of the batch column of this block.
+template <typename T>
+__device__ __forceinline__ T column_nu(const OpArgs<T>& A) { return A.nub ? A.nub[blockIdx.y] : A.L.nu; }
 
 // The reference tables are kernel parameters; indexing them with lane-dependent indices (a
 // quadrature point, a node) serialises the constant-bank reads, so the 3D kernels copy them to
@@ -136,6 +142,8 @@ __global__ void k_volume(OpArgs<T> A, Tab<T> tb_p, ColorInfo ci, int cpb) {
   const bool on = (g < cpb) && (cidx < ci.count);
   A.x += blockIdx.y * A.xs;
   A.y += blockIdx.y * A.ys;
+  if (A.state) A.state += blockIdx.y * A.ss;
+  const T nu = column_nu(A);
   int cc[3] = {0, 0, 0};
   if (on) decode_color_cell<D>(ci, cidx, cc);
   const LevelArgs<T>& L = A.L;
@@ -234,7 +242,7 @@ __global__ void k_volume(OpArgs<T> A, Tab<T> tb_p, ColorInfo ci, int cpb) {
       for (int c = 0; c < D; ++c)
         for (int l = 0; l < D; ++l) {
           T conv = RES ? v[c] * v[l] : dv[c] * v[l] + v[c] * dv[l];
-          F[c][l] = MASS ? (T)0 : L.nu * gp[c][l] - conv - ((c == l) ? pq : (T)0);
+          F[c][l] = MASS ? (T)0 : nu * gp[c][l] - conv - ((c == l) ? pq : (T)0);
         }
       for (int c = 0; c < D; ++c)
         for (int m = 0; m < D; ++m) {
@@ -379,6 +387,8 @@ __global__ void k_faces(OpArgs<T> A, Tab<T> tb_p, const int* __restrict__ bcells
   const LevelArgs<T>& L = A.L;
   A.x += blockIdx.y * A.xs;
   A.y += blockIdx.y * A.ys;
+  if (A.state) A.state += blockIdx.y * A.ss;
+  const T nu = column_nu(A);
   int cc[3] = {0, 0, 0};
   int64_t cell = 0;
   if (on) {
@@ -496,13 +506,13 @@ __global__ void k_faces(OpArgs<T> A, Tab<T> tb_p, const int* __restrict__ bcells
           const T wJ = tb.w[a] * JxWf;
           const T sgn = (y > 0) ? (T)1 : ((y < 0) ? (T)-1 : (T)0);
           for (int c = 0; c < D; ++c) {
-            T ac = -L.nu * dn[c] + L.nu * L.gamma1 / h * e[c] + L.gamma2 / h * en * nrm[c] + dp * nrm[c];
+            T ac = -nu * dn[c] + nu * L.gamma1 / h * e[c] + L.gamma2 / h * en * nrm[c] + dp * nrm[c];
             if (L.bconv) {
               if (RES) ac += (ypos - 2 * yneg) * v[c] + (T)0.5 * (fabs(gn) - gn) * gd[c];
               else ac += (ypos - 2 * yneg) * dv[c] + (T)0.5 * ((T)3 - sgn) * en * v[c];
             }
             s_a[c * NF + t] = wJ * ac;
-            const T bc = -wJ * L.nu * e[c];
+            const T bc = -wJ * nu * e[c];
             for (int m = 0; m < D; ++m) s_bg[(c * D + m) * NF + t] = bc * ghat[m];
           }
           s_s[t] = wJ * en;

@@ -53,6 +53,7 @@ __device__ __forceinline__ void face2d(const OpArgs<T>& A, const Tab<T>& tb, int
                                        int ty, int t, int cb, T vol, T* out, T& pout) {
   constexpr bool RES = (MODE == MR);
   const LevelArgs<T>& L = A.L;
+  const T nu = column_nu(A);
   const int kp1 = tb.k + 1, npc = tb.npc;
   const int e = side * (N - 1);
   const int tn = axis == 0 ? tx : ty;           // lane index along the normal direction
@@ -162,13 +163,13 @@ __device__ __forceinline__ void face2d(const OpArgs<T>& A, const Tab<T>& tb, int
   const T wJ = has ? tb.w[a] * JxWf : (T)0;
   T ac[2], bg[2][2];
   for (int c = 0; c < 2; ++c) {
-    T v = -L.nu * dn[c] + L.nu * L.gamma1 / h * ev[c] + L.gamma2 / h * en * nrm[c] + fp * nrm[c];
+    T v = -nu * dn[c] + nu * L.gamma1 / h * ev[c] + L.gamma2 / h * en * nrm[c] + fp * nrm[c];
     if (L.bconv) {
       if (RES) v += (ypos - 2 * yneg) * fs[c] + (T)0.5 * (fabs(gn) - gn) * gd[c];
       else v += (ypos - 2 * yneg) * fv[c] + (T)0.5 * ((T)3 - sgn) * en * fs[c];
     }
     ac[c] = wJ * v;
-    const T bc = -wJ * L.nu * ev[c];
+    const T bc = -wJ * nu * ev[c];
     bg[c][0] = bc * ghat[0];
     bg[c][1] = bc * ghat[1];
   }
@@ -229,6 +230,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_volume2d(OpArgs
   const bool on = (slot < CPW) && (cidx < ci.count);
   A.x += blockIdx.y * A.xs;
   A.y += blockIdx.y * A.ys;
+  if (A.state) A.state += blockIdx.y * A.ss;
+  const T nu = column_nu(A);
   const LevelArgs<T>& L = A.L;
   int cc[3] = {0, 0, 0};
   if (on) decode_color_cell<2>(ci, cidx, cc);
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_volume2d(OpArgs
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
       T conv = RES ? sq[c] * sq[l] : dq[c] * sq[l] + sq[c] * dq[l];
-      F[l] = MASS ? (T)0 : L.nu * gp[c][l] - conv - ((c == l) ? pq : (T)0);
+      F[l] = MASS ? (T)0 : nu * gp[c][l] - conv - ((c == l) ? pq : (T)0);
     }
 #pragma unroll
     for (int m = 0; m < 2; ++m) Fh[c][m] = wa * JxW * (G[m][0] * F[0] + G[m][1] * F[1]);

@@ -131,7 +131,7 @@ template <typename T, int N, int NX, int NPC>
 __device__ __forceinline__ void face_jac_tile(const Tab<T>& tb, const LevelArgs<T>& L, int axis, int side,
                                               const T* __restrict__ xs0, const T* __restrict__ xs1,
                                               const T* __restrict__ ss0, const T* __restrict__ ss1,
-                                              const T* pm, const T (&gc)[6], T vol, T wa,
+                                              const T* pm, const T (&gc)[6], T vol, T wa, T nu,
                                               T (&out)[2][N * N], T (&pacc)[NPC]) {
   const int e = side * (N - 1);
   const T* xsc[2] = {xs0, xs1};
@@ -173,7 +173,7 @@ __device__ __forceinline__ void face_jac_tile(const Tab<T>& tb, const LevelArgs<
     area += s * tb.qw[p];
   }
   const T h = vol / area * L.hscale;
-  const T pen1 = L.nu * L.gamma1 / h, pen2 = L.gamma2 / h;
+  const T pen1 = nu * L.gamma1 / h, pen2 = L.gamma2 / h;
   T tA[2][N], tB[2][N];
 #pragma unroll
   for (int c = 0; c < 2; ++c)
@@ -220,10 +220,10 @@ __device__ __forceinline__ void face_jac_tile(const Tab<T>& tb, const LevelArgs<
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const T nc = c == 0 ? n0 : n1;
-      T v = -L.nu * dn[c] + pen1 * fv[c] + pen2 * en * nc + fp * nc;
+      T v = -nu * dn[c] + pen1 * fv[c] + pen2 * en * nc + fp * nc;
       if (L.bconv) v += (ypos - 2 * yneg) * fv[c] + (T)0.5 * ((T)3 - sgn) * en * fs[c];
       ac[c] = wJ * v;
-      const T bc = -wJ * L.nu * fv[c];
+      const T bc = -wJ * nu * fv[c];
       bgn[c] = bc * (axis == 0 ? gh0 : gh1);            // normal reference direction
       bgt[c] = bc * (axis == 0 ? gh1 : gh0);            // along the face
     }
@@ -273,6 +273,11 @@ k_apply2d_tile(OpArgs<T> A, Tab<T> tb, const T* __restrict__ rhs, int tiles_x) {
   T* xs = reinterpret_cast<T*>(smraw);               // [KP1][2][NXY] increment
   T* ss = xs + KP1 * 2 * NXY;                        // [KP1][2][NXY] state
   const LevelArgs<T>& L = A.L;
+  // blockIdx.y: independent column of a batched apply (own increment, state, output, viscosity)
+  A.x += blockIdx.y * A.xs;
+  A.state += blockIdx.y * A.ss;
+  A.y += blockIdx.y * A.ys;
+  if (rhs) rhs += blockIdx.y * A.ys;
   const int n = L.n, N1 = L.N1;
   const int tix = blockIdx.x % tiles_x, tiy = blockIdx.x / tiles_x;
   const int cx0 = tix * (CX - 1) - 1, cy0 = tiy * (CY - 1) - 1;   // first computed cell
@@ -321,7 +326,7 @@ k_apply2d_tile(OpArgs<T> A, Tab<T> tb, const T* __restrict__ rhs, int tiles_x) {
   __syncthreads();
 
   const int nb = lcx * (N - 1) + NX * (lcy * (N - 1));   // the cell's first node in the tile
-  const T nu = L.nu;
+  const T nu = column_nu(A);
 #pragma unroll 1
   for (int a = 0; a < KP1; ++a) {
     const T wa = tb.w[a];
@@ -452,7 +457,7 @@ k_apply2d_tile(OpArgs<T> A, Tab<T> tb, const T* __restrict__ rhs, int tiles_x) {
           const int axis = f >> 1, side = f & 1;
           const int cc = axis == 0 ? cx : cy;
           if (side == 0 ? cc == 0 : cc == n - 1)
-            face_jac_tile<T, N, NX, NPC>(tb, L, axis, side, xa0, xa1, sa0, sa1, pm, gc, vol, wa, out, pacc);
+            face_jac_tile<T, N, NX, NPC>(tb, L, axis, side, xa0, xa1, sa0, sa1, pm, gc, vol, wa, nu, out, pacc);
         }
       }
     }
@@ -504,13 +509,14 @@ k_apply2d_tile(OpArgs<T> A, Tab<T> tb, const T* __restrict__ rhs, int tiles_x) {
 // Launch of the tiled apply for an N-node, KP1-time-node level.  Returns cudaErrorNotSupported
 // for configurations it does not cover (the caller then uses the colour-split kernels).
 template <typename T, int N, int KP1>
-cudaError_t launch_apply2d_tile(const OpArgs<T>& A, const Tab<T>& tb, const T* rhs, int n, cudaStream_t s) {
+cudaError_t launch_apply2d_tile(const OpArgs<T>& A, const Tab<T>& tb, const T* rhs, int n, cudaStream_t s,
+                                int columns = 1) {
   using TL = Tile2D<N>;
   const size_t smem = (size_t)2 * KP1 * 2 * TL::NXY * sizeof(T);
   cudaError_t e = allow_smem(k_apply2d_tile<T, N, KP1>, smem);
   if (e != cudaSuccess) return e;
   const int tx = (n + TL::CX - 2) / (TL::CX - 1), ty = (n + TL::CY - 2) / (TL::CY - 1);
-  k_apply2d_tile<T, N, KP1><<<(unsigned)(tx * ty), TL::THREADS, smem, s>>>(A, tb, rhs, tx);
+  k_apply2d_tile<T, N, KP1><<<dim3((unsigned)(tx * ty), columns), TL::THREADS, smem, s>>>(A, tb, rhs, tx);
   return cudaGetLastError();
 }
 

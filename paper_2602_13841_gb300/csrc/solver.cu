@@ -16,6 +16,7 @@
 
 #include "handle.hpp"
 #include "userdata.hpp"
+#include "group.hpp"
 #include "vec.cuh"
 #include "counters.hpp"
 
@@ -39,6 +40,7 @@ PhaseTimer::~PhaseTimer() { for (auto e : pool) cudaEventDestroy(e); }
 
 // ---------------------------------------------------------------------------- set-up
 cudaError_t Handle::ensure_mg() {
+  if (group) return cudaSuccess;                 // the group's hierarchy serves this handle
   if (precond_fp32()) {
     if (!mg32) { mg32.reset(new MG<float>()); cudaError_t e = mg32->allocate(this); if (e != cudaSuccess) { mg32.reset(); return e; } }
   } else {
@@ -133,6 +135,7 @@ static cudaError_t project_mean(Handle* h, double* U) {
 
 template <typename T>
 static cudaError_t precondition(Handle* h, MG<T>& mg, const double* v, double* z) {
+  if (h->group) return group_vcycle(h, v, z);
   const Level& L = h->levels[0];
   CKE((vcopy<double, T>(L.Nst, v, mg.r[0], h->stream)));
   if (h->timing) h->t_mg.begin(h->stream);
@@ -258,7 +261,7 @@ static double interp_step(double a1, double f1, bool have2, double a2, double f2
 template <typename T>
 static cudaError_t rebuild(Handle* h, MG<T>& mg, const double* X, stmg_stats* st) {
   if (h->timing) h->t_rebuild.begin(h->stream);
-  cudaError_t e = mg.setup(X);
+  cudaError_t e = h->group ? group_build(h, X) : mg.setup(X);
   if (h->timing) h->t_rebuild.end(h->stream);
   st->rebuilds++;
   return e;
@@ -377,7 +380,7 @@ stmg_status stmg_smoother_build(stmg_handle* hh, const double* U) {
   cudaError_t e = h->ensure_mg();
   if (e == cudaErrorNotSupported) return h->fail(STMG_ERR_UNSUPPORTED, "smoother_build: patch too large for this configuration");
   if (e != cudaSuccess) return h->fail(e == cudaErrorMemoryAllocation ? STMG_ERR_OOM : STMG_ERR_CUDA, std::string("smoother_build: ") + cudaGetErrorString(e));
-  e = h->precond_fp32() ? h->mg32->setup(U) : h->mg64->setup(U);
+  e = h->group ? group_build(h, U) : h->precond_fp32() ? h->mg32->setup(U) : h->mg64->setup(U);
   if (e == cudaErrorUnknown) return h->fail(STMG_ERR_NUMERIC, "smoother_build: singular patch or coarse matrix");
   if (e == cudaErrorNotSupported) return h->fail(STMG_ERR_UNSUPPORTED, "smoother_build: patch too large for this configuration");
   if (e != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string("smoother_build: ") + cudaGetErrorString(e));
@@ -387,6 +390,7 @@ stmg_status stmg_smoother_build(stmg_handle* hh, const double* U) {
 stmg_status stmg_smoother_sweep(stmg_handle* hh, int level, const void* rhs, void* d, int nsweeps, int zero_start) {
   if (!hh || !rhs || !d || nsweeps < 0) return STMG_ERR_ARG;
   Handle* h = H(hh);
+  if (h->group) return h->fail(STMG_ERR_ARG, "smoother_sweep: the handle is attached to a group");
   if (level < 0 || level + 1 >= (int)h->levels.size()) return h->fail(STMG_ERR_ARG, "smoother_sweep: level has no smoother");
   bool built = h->precond_fp32() ? (h->mg32 && h->mg32->built) : (h->mg64 && h->mg64->built);
   if (!built) return h->fail(STMG_ERR_ARG, "smoother_sweep: call stmg_smoother_build first");
@@ -401,6 +405,7 @@ stmg_status stmg_smoother_sweep(stmg_handle* hh, int level, const void* rhs, voi
 stmg_status stmg_vcycle(stmg_handle* hh, const double* r, double* z) {
   if (!hh || !r || !z) return STMG_ERR_ARG;
   Handle* h = H(hh);
+  if (h->group) return h->fail(STMG_ERR_ARG, "vcycle: the handle is attached to a group");
   bool built = h->precond_fp32() ? (h->mg32 && h->mg32->built) : (h->mg64 && h->mg64->built);
   if (!built) return h->fail(STMG_ERR_ARG, "vcycle: call stmg_smoother_build first");
   cudaError_t e = h->precond_fp32() ? precondition<float>(h, *h->mg32, r, z) : precondition<double>(h, *h->mg64, r, z);
@@ -413,6 +418,7 @@ stmg_status stmg_vcycle(stmg_handle* hh, const double* r, double* z) {
 stmg_status stmg_transfer(stmg_handle* hh, int level, int op, const void* in, void* out) {
   if (!hh || !in || !out) return STMG_ERR_ARG;
   Handle* h = H(hh);
+  if (h->group) return h->fail(STMG_ERR_ARG, "transfer: the handle is attached to a group");
   if (level < 0 || level + 1 >= (int)h->levels.size() || op < 0 || op > 2) return h->fail(STMG_ERR_ARG, "transfer: bad level or op");
   cudaError_t e = h->ensure_mg();
   if (e != cudaSuccess) return h->fail(STMG_ERR_CUDA, std::string("transfer: ") + cudaGetErrorString(e));
@@ -434,6 +440,7 @@ stmg_status stmg_transfer(stmg_handle* hh, int level, int op, const void* in, vo
 stmg_status stmg_level_state(stmg_handle* hh, int level, void* out) {
   if (!hh || !out) return STMG_ERR_ARG;
   Handle* h = H(hh);
+  if (h->group) return h->fail(STMG_ERR_ARG, "level_state: the handle is attached to a group");
   if (level < 0 || level >= (int)h->levels.size()) return h->fail(STMG_ERR_ARG, "level_state: bad level");
   bool built = h->precond_fp32() ? (h->mg32 && h->mg32->built) : (h->mg64 && h->mg64->built);
   if (!built) return h->fail(STMG_ERR_ARG, "level_state: call stmg_smoother_build first");
@@ -509,9 +516,17 @@ stmg_status stmg_slab_solve(stmg_handle* hh, double t_start, const double* V_pre
     cudaEventCreate(&e0); cudaEventCreate(&e1);
     cudaEventRecord(e0, h->stream);
   }
-  stmg_status rs = h->precond_fp32() ? newton<float>(h, *h->mg32, t_start, V_prev, U, S)
-                                     : newton<double>(h, *h->mg64, t_start, V_prev, U, S);
-  if (rs == STMG_OK || rs == STMG_ERR_NOT_CONVERGED) {
+  stmg_status rs;
+  if (h->group) {
+    group_enter(h);
+    rs = h->precond_fp32() ? newton<float>(h, *group_core_mg<float>(h), t_start, V_prev, U, S)
+                           : newton<double>(h, *group_core_mg<double>(h), t_start, V_prev, U, S);
+    group_leave(h);
+  } else {
+    rs = h->precond_fp32() ? newton<float>(h, *h->mg32, t_start, V_prev, U, S)
+                           : newton<double>(h, *h->mg64, t_start, V_prev, U, S);
+  }
+  if (!h->group && (rs == STMG_OK || rs == STMG_ERR_NOT_CONVERGED)) {
     const cudaError_t w = h->precond_fp32() ? h->mg32->check_wait() : h->mg64->check_wait();
     if (w == cudaErrorTimeout) rs = h->fail(STMG_ERR_TIMEOUT, "slab_solve: a bounded wait in the Vanka apply ran out");
     else if (w != cudaSuccess) rs = h->fail(STMG_ERR_CUDA, std::string("slab_solve: ") + cudaGetErrorString(w));

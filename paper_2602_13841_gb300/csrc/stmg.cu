@@ -16,6 +16,7 @@
 #include "counters.hpp"
 #include "handle.hpp"
 #include "userdata.hpp"
+#include "group.hpp"
 
 using namespace stmg;
 
@@ -228,6 +229,7 @@ stmg_status stmg_footprint(const stmg_params* p, uint64_t* bytes) {
 stmg_status stmg_set_physics(stmg_handle* hh, double nu, double tau, int problem) {
   if (!hh || !(nu > 0) || !(tau > 0) || problem < STMG_TG2D || problem > STMG_USER) return STMG_ERR_ARG;
   Handle* h = reinterpret_cast<Handle*>(hh);
+  if (h->group && tau != h->pb.tau) return h->fail(STMG_ERR_ARG, "set_physics: an attached handle keeps its group's tau");
   h->prm.nu = nu; h->prm.tau = tau; h->prm.problem = problem;
   h->pb.nu = nu; h->pb.tau = tau; h->pb.problem = problem;
   h->pb.ftab = problem == STMG_USER ? h->ftab : nullptr;
@@ -328,6 +330,8 @@ stmg_status stmg_kernel_profile_reset(stmg_handle* hh) {
 }
 
 void stmg_destroy(stmg_handle* hh) {
+  if (!hh) return;
+  group_forget(reinterpret_cast<Handle*>(hh));
   delete reinterpret_cast<Handle*>(hh);
 }
 

@@ -57,7 +57,7 @@ static std::vector<double> node_positions(int n, int r, double scale) {
   return x;
 }
 
-void build_transfer(Handle* h, Transfer& tr, const Level& f, const Level& c, size_t esize) {
+void build_transfer(Handle* h, Transfer& tr, const Level& f, const Level& c, size_t esize, int nb) {
   tr.fine = &f; tr.coarse = &c;
   const double cf = (double)c.n / f.n;
   auto R = eval_rows(c.n, c.r, node_positions(f.n, f.r, cf));
@@ -118,9 +118,11 @@ void build_transfer(Handle* h, Transfer& tr, const Level& f, const Level& c, siz
   int64_t big = (int64_t)(f.k + 1) * f.Nv;
   int64_t pbig = (int64_t)(f.k + 1) * f.Np;
   if (pbig > big) big = pbig;
-  tr.tmpA = h->dalloc(big * esize);
-  tr.tmpB = h->dalloc(big * esize);
-  tr.tmpC = h->dalloc(big * esize);
+  tr.nb = nb;
+  tr.scr = big;
+  tr.tmpA = h->dalloc((size_t)nb * big * esize);
+  tr.tmpB = h->dalloc((size_t)nb * big * esize);
+  tr.tmpC = h->dalloc((size_t)nb * big * esize);
 }
 
 // ---------------------------------------------------------------------------- kernels
@@ -129,11 +131,11 @@ void build_transfer(Handle* h, Transfer& tr, const Level& f, const Level& c, siz
 template <typename T>
 __global__ void k_axis(const T* __restrict__ in, T* __restrict__ out, int nin, int nout, int64_t inner,
                        int64_t outer, int64_t sin, int64_t sout, const int* __restrict__ rowptr,
-                       const int* __restrict__ col, const T* __restrict__ val) {
+                       const int* __restrict__ col, const T* __restrict__ val, int64_t zin, int64_t zout) {
   const int b = blockIdx.y;
   const int64_t total = outer * nout * inner;
-  in += b * sin;
-  out += b * sout;
+  in += b * sin + blockIdx.z * zin;           // blockIdx.z: independent slot
+  out += b * sout + blockIdx.z * zout;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     int64_t p = idx % inner;
@@ -150,7 +152,9 @@ __global__ void k_axis(const T* __restrict__ in, T* __restrict__ out, int nin, i
 struct Mat3 { double m[MAXKP1][MAXKP1]; };
 template <typename T>
 __global__ void k_timemix(const T* __restrict__ in, T* __restrict__ out, int64_t L, int nin, int nout,
-                          int64_t sin, int64_t sout, Mat3 M) {
+                          int64_t sin, int64_t sout, Mat3 M, int64_t zin, int64_t zout) {
+  in += blockIdx.y * zin;                     // blockIdx.y: independent slot
+  out += blockIdx.y * zout;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x) {
     T v[MAXKP1];
     for (int a = 0; a < nin; ++a) v[a] = in[a * sin + i];
@@ -165,9 +169,9 @@ __global__ void k_timemix(const T* __restrict__ in, T* __restrict__ out, int64_t
 // Pressure prolongation: fine cell cf, mode mf  <-  coarse cell, all coarse modes (per time node)
 template <typename T, int D>
 __global__ void k_pprolong(const T* __restrict__ in, T* __restrict__ out, int nf, int ratio, int npf, int npc,
-                           const T* __restrict__ PT, int64_t sin, int64_t sout) {
+                           const T* __restrict__ PT, int64_t sin, int64_t sout, int64_t zin, int64_t zout) {
   const int b = blockIdx.y;
-  in += b * sin; out += b * sout;
+  in += b * sin + blockIdx.z * zin; out += b * sout + blockIdx.z * zout;
   int64_t ncf = 1;
   for (int l = 0; l < D; ++l) ncf *= nf;
   const int nc = nf / ratio;
@@ -191,9 +195,9 @@ __global__ void k_pprolong(const T* __restrict__ in, T* __restrict__ out, int nf
 // Pressure restriction (transpose): coarse cell, mode mc  <-  its fine cells, all fine modes
 template <typename T, int D>
 __global__ void k_prestrict(const T* __restrict__ in, T* __restrict__ out, int nf, int ratio, int npf, int npc,
-                            const T* __restrict__ PT, int64_t sin, int64_t sout) {
+                            const T* __restrict__ PT, int64_t sin, int64_t sout, int64_t zin, int64_t zout) {
   const int b = blockIdx.y;
-  in += b * sin; out += b * sout;
+  in += b * sin + blockIdx.z * zin; out += b * sout + blockIdx.z * zout;
   const int nc = nf / ratio;
   int64_t ncc = 1;
   for (int l = 0; l < D; ++l) ncc *= nc;
@@ -230,9 +234,11 @@ template <> const double* ptab<double>(const Transfer& t) { return t.PT64; }
 template <> const float* ptab<float>(const Transfer& t) { return t.PT32; }
 
 // Apply a 1D operator along every axis to `batch` arrays of nin^d entries -> nout^d entries.
+// `slots` independent inputs at in + j * zin (outputs out + j * zout, scratch t + j * zt).
 template <typename T>
 static cudaError_t tensor_apply(const Csr1D& op, int d, int nin, int nout, int batch, const T* in, T* out,
-                                T* t1, T* t2, cudaStream_t s) {
+                                T* t1, T* t2, cudaStream_t s, int slots = 1, int64_t zin = 0, int64_t zout = 0,
+                                int64_t zt = 0) {
   int64_t ext[3] = {nin, nin, nin};
   const T* src = in;
   int64_t sin = 1;
@@ -247,8 +253,10 @@ static cudaError_t tensor_apply(const Csr1D& op, int d, int nin, int nout, int b
     int64_t sdst = (ax == d - 1) ? 0 : sout;
     // the final pass writes with the caller's stride (= nout^d)
     if (ax == d - 1) sdst = sout;
-    dim3 grid(grid1(outer * nout * inner), batch);
-    k_axis<T><<<grid, 256, 0, s>>>(src, dst, (int)ext[ax], nout, inner, outer, sin, sdst, op.rowptr, op.col, vals<T>(op));
+    dim3 grid(grid1(outer * nout * inner), batch, slots);
+    const int64_t zs = (ax == 0) ? zin : zt, zd = (ax == d - 1) ? zout : zt;
+    k_axis<T><<<grid, 256, 0, s>>>(src, dst, (int)ext[ax], nout, inner, outer, sin, sdst, op.rowptr, op.col,
+                                   vals<T>(op), zs, zd);
     note_launch();
     ext[ax] = nout;
     src = dst;
@@ -258,49 +266,51 @@ static cudaError_t tensor_apply(const Csr1D& op, int d, int nin, int nout, int b
 }
 
 template <typename T>
-cudaError_t Transfer::prolong(const T* xc, T* xf, cudaStream_t s) const {
+cudaError_t Transfer::prolong(const T* xc, T* xf, cudaStream_t s, int slots) const {
   const Level& f = *fine; const Level& c = *coarse;
+  if (slots < 1 || slots > nb) return cudaErrorInvalidValue;
   T* A = (T*)tmpA; T* B = (T*)tmpB; T* C = (T*)tmpC;
   const int d = f.d;
   // velocity: space at coarse time nodes -> C, then time mix into xf
-  cudaError_t e = tensor_apply<T>(P1, d, c.N1, f.N1, (c.k + 1) * d, xc, C, A, B, s);
+  cudaError_t e = tensor_apply<T>(P1, d, c.N1, f.N1, (c.k + 1) * d, xc, C, A, B, s, slots, c.Nst, scr, scr);
   if (e != cudaSuccess) return e;
   Mat3 M{};
   for (int a = 0; a <= f.k; ++a) for (int b = 0; b <= c.k; ++b) M.m[a][b] = E[a][b];
-  k_timemix<T><<<grid1(f.Nv), 256, 0, s>>>(C, xf, f.Nv, c.k + 1, f.k + 1, f.Nv, f.Nv, M);
+  k_timemix<T><<<dim3(grid1(f.Nv), slots), 256, 0, s>>>(C, xf, f.Nv, c.k + 1, f.k + 1, f.Nv, f.Nv, M, scr, f.Nst);
   note_launch();
   // pressure
   const T* pc = xc + (int64_t)(c.k + 1) * c.Nv;
   T* pf = xf + (int64_t)(f.k + 1) * f.Nv;
   int64_t ncf = f.Np / f.npc;
-  dim3 g(grid1(ncf * f.npc), c.k + 1);
-  if (d == 2) k_pprolong<T, 2><<<g, 256, 0, s>>>(pc, C, f.n, ratio, f.npc, c.npc, ptab<T>(*this), c.Np, f.Np);
-  else k_pprolong<T, 3><<<g, 256, 0, s>>>(pc, C, f.n, ratio, f.npc, c.npc, ptab<T>(*this), c.Np, f.Np);
+  dim3 g(grid1(ncf * f.npc), c.k + 1, slots);
+  if (d == 2) k_pprolong<T, 2><<<g, 256, 0, s>>>(pc, C, f.n, ratio, f.npc, c.npc, ptab<T>(*this), c.Np, f.Np, c.Nst, scr);
+  else k_pprolong<T, 3><<<g, 256, 0, s>>>(pc, C, f.n, ratio, f.npc, c.npc, ptab<T>(*this), c.Np, f.Np, c.Nst, scr);
   note_launch();
-  k_timemix<T><<<grid1(f.Np), 256, 0, s>>>(C, pf, f.Np, c.k + 1, f.k + 1, f.Np, f.Np, M);
+  k_timemix<T><<<dim3(grid1(f.Np), slots), 256, 0, s>>>(C, pf, f.Np, c.k + 1, f.k + 1, f.Np, f.Np, M, scr, f.Nst);
   note_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Transfer::restrict_(const T* xf, T* xc, cudaStream_t s) const {
+cudaError_t Transfer::restrict_(const T* xf, T* xc, cudaStream_t s, int slots) const {
   const Level& f = *fine; const Level& c = *coarse;
+  if (slots < 1 || slots > nb) return cudaErrorInvalidValue;
   T* A = (T*)tmpA; T* B = (T*)tmpB; T* C = (T*)tmpC;
   const int d = f.d;
   Mat3 M{};
   for (int a = 0; a <= c.k; ++a) for (int b = 0; b <= f.k; ++b) M.m[a][b] = E[b][a];   // E^T
-  k_timemix<T><<<grid1(f.Nv), 256, 0, s>>>(xf, C, f.Nv, f.k + 1, c.k + 1, f.Nv, f.Nv, M);
+  k_timemix<T><<<dim3(grid1(f.Nv), slots), 256, 0, s>>>(xf, C, f.Nv, f.k + 1, c.k + 1, f.Nv, f.Nv, M, f.Nst, scr);
   note_launch();
-  cudaError_t e = tensor_apply<T>(P1T, d, f.N1, c.N1, (c.k + 1) * d, C, xc, A, B, s);
+  cudaError_t e = tensor_apply<T>(P1T, d, f.N1, c.N1, (c.k + 1) * d, C, xc, A, B, s, slots, scr, c.Nst, scr);
   if (e != cudaSuccess) return e;
   const T* pf = xf + (int64_t)(f.k + 1) * f.Nv;
   T* pc = xc + (int64_t)(c.k + 1) * c.Nv;
-  k_timemix<T><<<grid1(f.Np), 256, 0, s>>>(pf, C, f.Np, f.k + 1, c.k + 1, f.Np, f.Np, M);
+  k_timemix<T><<<dim3(grid1(f.Np), slots), 256, 0, s>>>(pf, C, f.Np, f.k + 1, c.k + 1, f.Np, f.Np, M, f.Nst, scr);
   note_launch();
   int64_t ncc = c.Np / c.npc;
-  dim3 g(grid1(ncc * c.npc), c.k + 1);
-  if (d == 2) k_prestrict<T, 2><<<g, 256, 0, s>>>(C, pc, f.n, ratio, f.npc, c.npc, ptab<T>(*this), f.Np, c.Np);
-  else k_prestrict<T, 3><<<g, 256, 0, s>>>(C, pc, f.n, ratio, f.npc, c.npc, ptab<T>(*this), f.Np, c.Np);
+  dim3 g(grid1(ncc * c.npc), c.k + 1, slots);
+  if (d == 2) k_prestrict<T, 2><<<g, 256, 0, s>>>(C, pc, f.n, ratio, f.npc, c.npc, ptab<T>(*this), f.Np, c.Np, scr, c.Nst);
+  else k_prestrict<T, 3><<<g, 256, 0, s>>>(C, pc, f.n, ratio, f.npc, c.npc, ptab<T>(*this), f.Np, c.Np, scr, c.Nst);
   note_launch();
   return cudaGetLastError();
 }
@@ -311,15 +321,15 @@ cudaError_t Transfer::interp_state(const T* Vf, T* Vc, cudaStream_t s) const {
   T* A = (T*)tmpA; T* B = (T*)tmpB; T* C = (T*)tmpC;
   Mat3 M{};
   for (int a = 0; a <= c.k; ++a) for (int b = 0; b <= f.k; ++b) M.m[a][b] = Et[a][b];
-  k_timemix<T><<<grid1(f.Nv), 256, 0, s>>>(Vf, C, f.Nv, f.k + 1, c.k + 1, f.Nv, f.Nv, M);
+  k_timemix<T><<<grid1(f.Nv), 256, 0, s>>>(Vf, C, f.Nv, f.k + 1, c.k + 1, f.Nv, f.Nv, M, 0, 0);
   note_launch();
   return tensor_apply<T>(I1, f.d, f.N1, c.N1, (c.k + 1) * f.d, C, Vc, A, B, s);
 }
 
-template cudaError_t Transfer::prolong<float>(const float*, float*, cudaStream_t) const;
-template cudaError_t Transfer::prolong<double>(const double*, double*, cudaStream_t) const;
-template cudaError_t Transfer::restrict_<float>(const float*, float*, cudaStream_t) const;
-template cudaError_t Transfer::restrict_<double>(const double*, double*, cudaStream_t) const;
+template cudaError_t Transfer::prolong<float>(const float*, float*, cudaStream_t, int) const;
+template cudaError_t Transfer::prolong<double>(const double*, double*, cudaStream_t, int) const;
+template cudaError_t Transfer::restrict_<float>(const float*, float*, cudaStream_t, int) const;
+template cudaError_t Transfer::restrict_<double>(const double*, double*, cudaStream_t, int) const;
 template cudaError_t Transfer::interp_state<float>(const float*, float*, cudaStream_t) const;
 template cudaError_t Transfer::interp_state<double>(const double*, double*, cudaStream_t) const;
 

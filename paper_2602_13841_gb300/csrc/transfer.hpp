@@ -33,21 +33,25 @@ struct Transfer {
   int ntypes = 1, ratio = 1;    // pressure child types (2^d for h-transfers)
   double* PT64 = nullptr;       // [ntypes][npf][npc]
   float* PT32 = nullptr;
-  // scratch (element type of the preconditioner)
+  // scratch (element type of the preconditioner), `nb` slots of `scr` entries each
   void* tmpA = nullptr;
   void* tmpB = nullptr;
   void* tmpC = nullptr;
+  int nb = 1;                   // slots: independent vectors transferred by one launch each
+  int64_t scr = 0;
 
+  // Each call transfers `slots` independent vectors (slot j at offset j * n_st of its level;
+  // slots <= nb), in the same launches.
   template <typename T>
-  cudaError_t prolong(const T* xc, T* xf, cudaStream_t s) const;     // xf = P xc
+  cudaError_t prolong(const T* xc, T* xf, cudaStream_t s, int slots = 1) const;     // xf = P xc
   template <typename T>
-  cudaError_t restrict_(const T* xf, T* xc, cudaStream_t s) const;   // xc = P^T xf
+  cudaError_t restrict_(const T* xf, T* xc, cudaStream_t s, int slots = 1) const;   // xc = P^T xf
   template <typename T>
-  cudaError_t interp_state(const T* Vf, T* Vc, cudaStream_t s) const; // velocity part only
+  cudaError_t interp_state(const T* Vf, T* Vc, cudaStream_t s) const; // velocity part only, one slot
 };
 
 struct Handle;
-// Build the transfer between levels[l] and levels[l+1]; scratch for element size `esize`.
-void build_transfer(Handle* h, Transfer& tr, const Level& fine, const Level& coarse, size_t esize);
+// Build the transfer between levels[l] and levels[l+1]; scratch for element size `esize` and nb slots.
+void build_transfer(Handle* h, Transfer& tr, const Level& fine, const Level& coarse, size_t esize, int nb = 1);
 
 }  // namespace stmg

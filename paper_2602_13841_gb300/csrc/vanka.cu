@@ -11,7 +11,7 @@ namespace stmg {
                                                     void*, float*, int*, T*, cudaStream_t);                       \
   extern template cudaError_t vanka_apply_dim<T, D>(const Level&, const Problem&, const T*, const void*,         \
                                                     const float*, const T*, T*, double, double, int, int*,       \
-                                                    cudaStream_t, unsigned);
+                                                    cudaStream_t, unsigned, int);
 STMG_EXTERN(float, 2)
 STMG_EXTERN(double, 2)
 STMG_EXTERN(float, 3)
@@ -87,9 +87,9 @@ cudaError_t vanka_build(const Level& lv, const Problem& pb, const T* U, T* vstar
 template <typename T>
 cudaError_t vanka_apply(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
                         const T* res, T* d, double omega, double omega_p, int color, int* wstat, cudaStream_t s,
-                        unsigned extra_tx) {
-  return lv.d == 2 ? vanka_apply_dim<T, 2>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, wstat, s, extra_tx)
-                   : vanka_apply_dim<T, 3>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, wstat, s, extra_tx);
+                        unsigned extra_tx, int slots) {
+  return lv.d == 2 ? vanka_apply_dim<T, 2>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, wstat, s, extra_tx, slots)
+                   : vanka_apply_dim<T, 3>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, wstat, s, extra_tx, slots);
 }
 
 template cudaError_t vanka_build<float>(const Level&, const Problem&, const float*, float*, float*, float*, float*,
@@ -97,8 +97,8 @@ template cudaError_t vanka_build<float>(const Level&, const Problem&, const floa
 template cudaError_t vanka_build<double>(const Level&, const Problem&, const double*, double*, double*, double*,
                                          double*, double*, void*, float*, int*, double*, cudaStream_t);
 template cudaError_t vanka_apply<float>(const Level&, const Problem&, const float*, const void*, const float*,
-                                        const float*, float*, double, double, int, int*, cudaStream_t, unsigned);
+                                        const float*, float*, double, double, int, int*, cudaStream_t, unsigned, int);
 template cudaError_t vanka_apply<double>(const Level&, const Problem&, const double*, const void*, const float*,
-                                         const double*, double*, double, double, int, int*, cudaStream_t, unsigned);
+                                         const double*, double*, double, double, int, int*, cudaStream_t, unsigned, int);
 
 }  // namespace stmg

@@ -684,10 +684,18 @@ __host__ __device__ inline size_t apply_slot_bytes(int kp1, int ms, size_t si, s
   return (apply_smem_bytes(kp1, ms, si, t) + 127) & ~(size_t)127;
 }
 
+// Slot strides of a batched sweep (blockIdx.y = slot): inverse entries, FP16 scales, vector entries.
+struct SlotStrides { int64_t inv, scale, vec; };
+
 template <typename T, typename SI, int D, int N>
 __global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const float* __restrict__ scale,
                               const T* __restrict__ res, T* __restrict__ d, T omega, T omega_p, int kp1, int npc,
-                              TEig<T> te, ColorInfo ci, int* __restrict__ wstat, unsigned extra_tx) {
+                              TEig<T> te, ColorInfo ci, int* __restrict__ wstat, unsigned extra_tx,
+                              SlotStrides zs) {
+  inv += blockIdx.y * zs.inv;
+  if (scale) scale += blockIdx.y * zs.scale;
+  res += blockIdx.y * zs.vec;
+  d += blockIdx.y * zs.vec;
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int ms = MV + npc, st = inv_stride(ms, (int)sizeof(SI)), mr = (ms + 1) & ~1;
@@ -822,7 +830,11 @@ template <> struct InvLdG<__half> {
 template <typename T, typename SI, int D, int N>
 __global__ void k_vanka_apply_global(LevelArgs<T> L, const SI* __restrict__ inv, const float* __restrict__ scale,
                                      const T* __restrict__ res, T* __restrict__ d, T omega, T omega_p, int kp1,
-                                     int npc, TEig<T> te, ColorInfo ci) {
+                                     int npc, TEig<T> te, ColorInfo ci, SlotStrides zs) {
+  inv += blockIdx.y * zs.inv;
+  if (scale) scale += blockIdx.y * zs.scale;
+  res += blockIdx.y * zs.vec;
+  d += blockIdx.y * zs.vec;
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int ms = MV + npc, st = inv_stride(ms, (int)sizeof(SI)), mr = (ms + 1) & ~1;

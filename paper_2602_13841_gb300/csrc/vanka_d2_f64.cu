@@ -7,6 +7,6 @@ namespace stmg {
 template cudaError_t vanka_build_dim<double, 2>(const Level&, const Problem&, const double*, double*, double*, double*, double*, double*,
                                               void*, float*, int*, double*, cudaStream_t);
 template cudaError_t vanka_apply_dim<double, 2>(const Level&, const Problem&, const double*, const void*, const float*,
-                                              const double*, double*, double, double, int, int*, cudaStream_t, unsigned);
+                                              const double*, double*, double, double, int, int*, cudaStream_t, unsigned, int);
 
 }  // namespace stmg

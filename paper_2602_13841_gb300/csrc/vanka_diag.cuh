@@ -138,7 +138,11 @@ __host__ __device__ inline size_t diag_slot_bytes(int mv, int npc, int kp1, size
 // velocity, omega_p on pressure DoFs).  One warp per cell, CPB cells per block.
 template <typename T, int D, int N>
 __global__ void k_vanka_apply_diag(LevelArgs<T> L, const T* __restrict__ blobs, const T* __restrict__ res,
-                                   T* __restrict__ d, T omega, T omega_p, Tab<T> tb, ColorInfo ci, int cpb) {
+                                   T* __restrict__ d, T omega, T omega_p, Tab<T> tb, ColorInfo ci, int cpb,
+                                   SlotStrides zs) {
+  blobs += blockIdx.y * zs.inv;
+  res += blockIdx.y * zs.vec;
+  d += blockIdx.y * zs.vec;
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int npc = tb.npc, kp1 = tb.k + 1, ns = kp1 * npc, ms = MV + npc;

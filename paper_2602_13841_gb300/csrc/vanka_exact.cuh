@@ -123,7 +123,10 @@ __host__ __device__ inline size_t apply_exact_smem(int mst, int ms, size_t t) {
 template <typename T, int D, int N>
 __global__ void k_vanka_apply_exact(LevelArgs<T> L, const T* __restrict__ inv, const T* __restrict__ res,
                                     T* __restrict__ d, T omega, T omega_p, int kp1, int npc, ColorInfo ci,
-                                    int* __restrict__ wstat, unsigned extra_tx) {
+                                    int* __restrict__ wstat, unsigned extra_tx, SlotStrides zs) {
+  inv += blockIdx.y * zs.inv;
+  res += blockIdx.y * zs.vec;
+  d += blockIdx.y * zs.vec;
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int ms = MV + npc, mst = kp1 * ms, st = inv_stride(mst, (int)sizeof(T));

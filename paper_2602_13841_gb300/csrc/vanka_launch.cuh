@@ -174,16 +174,16 @@ static cudaError_t build_dn(const Level& lv, const Problem& pb, const T* U, T* v
 template <typename T, typename SI, int D, int N>
 static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv, const float* scale, const T* res,
                                T* d, double omega, double omega_p, const ColorInfo& ci, int* wstat,
-                               unsigned extra_tx, cudaStream_t s) {
+                               unsigned extra_tx, cudaStream_t s, int slots, SlotStrides zs) {
   // one block per cell, threads = spatial patch rows rounded up to whole warps
   const int ms = (int)vanka_spatial_size(lv), kp1 = lv.k + 1;
   const int threads = ((ms + 31) / 32) * 32;
   if (!apply_onchip(lv, sizeof(SI), sizeof(T))) {
     const int mr = (ms + 1) & ~1;
     const size_t gsm = (((size_t)kp1 * mr * sizeof(T) + 7) & ~(size_t)7) + (size_t)ms * 8;
-    k_vanka_apply_global<T, SI, D, N><<<(unsigned)ci.count, threads, gsm, s>>>(
+    k_vanka_apply_global<T, SI, D, N><<<dim3((unsigned)ci.count, slots), threads, gsm, s>>>(
         level_args<T>(lv, pb, 0.0), inv, scale, res, d, (T)omega, (T)omega_p, kp1, lv.npc,
-        make_teig<T>(lv.tabs, pb.tau), ci);
+        make_teig<T>(lv.tabs, pb.tau), ci, zs);
     return cudaSuccess;
   }
   // cells per block: 4 for one-warp patches (32 resident blocks per SM), else 1
@@ -194,25 +194,28 @@ static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv
   cudaError_t e = allow_smem(k_vanka_apply<T, SI, D, N>, smem);
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((ci.count + cpb - 1) / cpb);
-  k_vanka_apply<T, SI, D, N><<<blocks, threads * cpb, smem, s>>>(level_args<T>(lv, pb, 0.0), inv, scale, res, d,
-                                                                       (T)omega, (T)omega_p, kp1, lv.npc,
-                                                                       make_teig<T>(lv.tabs, pb.tau), ci, wstat, extra_tx);
+  k_vanka_apply<T, SI, D, N><<<dim3(blocks, slots), threads * cpb, smem, s>>>(
+      level_args<T>(lv, pb, 0.0), inv, scale, res, d, (T)omega, (T)omega_p, kp1, lv.npc,
+      make_teig<T>(lv.tabs, pb.tau), ci, wstat, extra_tx, zs);
   return cudaSuccess;
 }
 
 template <typename T, int D, int N>
 static cudaError_t apply_dn(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
                             const T* res, T* d, double omega, double omega_p, int color, int* wstat,
-                            unsigned extra_tx, cudaStream_t s) {
+                            unsigned extra_tx, cudaStream_t s, int slots) {
   const ColorInfo& ci = lv.colors[color];
   if (ci.count == 0) return cudaSuccess;
+  const int64_t cells = lv.Np / lv.npc;
+  const SlotStrides zs{cells * (int64_t)vanka_inv_entries(lv, invh ? 2 : (int)sizeof(T)), cells * (lv.k + 1),
+                       lv.Nst};
   if (lv.smoother == 2) {
     const int ms = (int)vanka_spatial_size(lv), mst = (lv.k + 1) * ms;
     const size_t smem = apply_exact_smem(mst, ms, sizeof(T));
     cudaError_t e = allow_smem(k_vanka_apply_exact<T, D, N>, smem);
     if (e != cudaSuccess) return e;
-    k_vanka_apply_exact<T, D, N><<<(unsigned)ci.count, ((mst + 31) / 32) * 32, smem, s>>>(
-        level_args<T>(lv, pb, 0.0), inv, res, d, (T)omega, (T)omega_p, lv.k + 1, lv.npc, ci, wstat, extra_tx);
+    k_vanka_apply_exact<T, D, N><<<dim3((unsigned)ci.count, slots), ((mst + 31) / 32) * 32, smem, s>>>(
+        level_args<T>(lv, pb, 0.0), inv, res, d, (T)omega, (T)omega_p, lv.k + 1, lv.npc, ci, wstat, extra_tx, zs);
     note_launch();
     return cudaGetLastError();
   }
@@ -225,15 +228,15 @@ static cudaError_t apply_dn(const Level& lv, const Problem& pb, const T* inv, co
     const size_t smem = (size_t)cpb * slot;
     cudaError_t e = allow_smem(k_vanka_apply_diag<T, D, N>, smem);
     if (e != cudaSuccess) return e;
-    k_vanka_apply_diag<T, D, N><<<(unsigned)((ci.count + cpb - 1) / cpb), 32 * cpb, smem, s>>>(
-        level_args<T>(lv, pb, 0.0), inv, res, d, (T)omega, (T)omega_p, make_tab<T>(lv.tabs, pb.tau), ci, cpb);
+    k_vanka_apply_diag<T, D, N><<<dim3((unsigned)((ci.count + cpb - 1) / cpb), slots), 32 * cpb, smem, s>>>(
+        level_args<T>(lv, pb, 0.0), inv, res, d, (T)omega, (T)omega_p, make_tab<T>(lv.tabs, pb.tau), ci, cpb, zs);
     note_launch();
     return cudaGetLastError();
   }
   cudaError_t e = invh ? apply_cells<T, __half, D, N>(lv, pb, (const __half*)invh, scale, res, d, omega, omega_p, ci,
-                                                      wstat, extra_tx, s)
+                                                      wstat, extra_tx, s, slots, zs)
                        : apply_cells<T, T, D, N>(lv, pb, inv, nullptr, res, d, omega, omega_p, ci, wstat, extra_tx,
-                                                 s);
+                                                 s, slots, zs);
   if (e != cudaSuccess) return e;
   note_launch();
   return cudaGetLastError();
@@ -254,11 +257,11 @@ cudaError_t vanka_build_dim(const Level& lv, const Problem& pb, const T* U, T* v
 template <typename T, int D>
 cudaError_t vanka_apply_dim(const Level& lv, const Problem& pb, const T* inv, const void* invh, const float* scale,
                             const T* res, T* d, double omega, double omega_p, int color, int* wstat, cudaStream_t s,
-                            unsigned extra_tx) {
+                            unsigned extra_tx, int slots) {
   const int N = lv.r + 2;
-  if (N == 3) return apply_dn<T, D, 3>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, wstat, extra_tx, s);
-  if (N == 4) return apply_dn<T, D, 4>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, wstat, extra_tx, s);
-  if (N == 5) return apply_dn<T, D, 5>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, wstat, extra_tx, s);
+  if (N == 3) return apply_dn<T, D, 3>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, wstat, extra_tx, s, slots);
+  if (N == 4) return apply_dn<T, D, 4>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, wstat, extra_tx, s, slots);
+  if (N == 5) return apply_dn<T, D, 5>(lv, pb, inv, invh, scale, res, d, omega, omega_p, color, wstat, extra_tx, s, slots);
   return cudaErrorNotSupported;
 }
 

@@ -38,6 +38,21 @@ cudaError_t vcopy(int64_t n, const S* x, T* y, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename S, typename T>
+__global__ void k_copy_slots(int64_t n, const S* __restrict__ x, int64_t xs, T* __restrict__ y, int64_t ys) {
+  x += blockIdx.y * xs;
+  y += blockIdx.y * ys;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (T)x[i];
+}
+
+template <typename S, typename T>
+cudaError_t vcopy_slots(int64_t n, int slots, const S* x, int64_t xs, T* y, int64_t ys, cudaStream_t s) {
+  k_copy_slots<S, T><<<dim3(grid_for(n), slots), 256, 0, s>>>(n, x, xs, y, ys);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // Partial dot products of up to DOTS_PER_ROW basis vectors with w per block: w[i] is read once
 // for all of them.  Each thread accumulates its strided elements in index order, then the block
 // reduces in a fixed tree: the result does not depend on how many vectors share a block.
@@ -197,6 +212,9 @@ template cudaError_t vcopy<double, float>(int64_t, const double*, float*, cudaSt
 template cudaError_t vcopy<float, double>(int64_t, const float*, double*, cudaStream_t);
 template cudaError_t vcopy<double, double>(int64_t, const double*, double*, cudaStream_t);
 template cudaError_t vcopy<float, float>(int64_t, const float*, float*, cudaStream_t);
+template cudaError_t vcopy_slots<double, float>(int64_t, int, const double*, int64_t, float*, int64_t, cudaStream_t);
+template cudaError_t vcopy_slots<float, double>(int64_t, int, const float*, int64_t, double*, int64_t, cudaStream_t);
+template cudaError_t vcopy_slots<double, double>(int64_t, int, const double*, int64_t, double*, int64_t, cudaStream_t);
 template cudaError_t vdots<float>(int64_t, int, const float*, int64_t, const float*, double*, double*, cudaStream_t);
 template cudaError_t vdots<double>(int64_t, int, const double*, int64_t, const double*, double*, double*, cudaStream_t);
 template cudaError_t vsub_comb<float>(int64_t, int, const float*, int64_t, const double*, float*, cudaStream_t);

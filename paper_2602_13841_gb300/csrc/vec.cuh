@@ -15,6 +15,9 @@ cudaError_t vaxpby(int64_t n, T a, const T* x, T b, T* y, cudaStream_t s);
 // y = x (element type conversion allowed)
 template <typename S, typename T>
 cudaError_t vcopy(int64_t n, const S* x, T* y, cudaStream_t s);
+// y_j = x_j (n entries) for j < slots, x_j = x + j xs, y_j = y + j ys (one launch)
+template <typename S, typename T>
+cudaError_t vcopy_slots(int64_t n, int slots, const S* x, int64_t xs, T* y, int64_t ys, cudaStream_t s);
 // out[l] = sum_i X[l*ldx + i] * w[i], l < m  (device scalars, double); scratch >= m*RED_BLOCKS doubles
 template <typename T>
 cudaError_t vdots(int64_t n, int m, const T* X, int64_t ldx, const T* w, double* out, double* scratch,

@@ -8,8 +8,11 @@ that still wait (backfilling), so work keeps flowing while big requests wait for
 worker thread owns a CUDA stream and keeps its last handle resident: a request of the same
 shape (d, n, r, k) reuses the hierarchy and work space (stmg_set_physics), and a free worker
 that holds the request's shape is preferred.  The solves of different workers overlap on the
-device.  All kernels are deterministic (fixed reduction order, coloured scatter), so a
-request's result is bitwise the same alone and in the mix.
+device.  With batching on (default), the handles of one shape held by different workers attach
+to a shared group (stmg_group_*): while several requests of that shape are being solved, their
+V-cycles run as batched launches (one launch per kernel for all of them).  All kernels are
+deterministic (fixed reduction order, coloured scatter) and a batched slot computes what a lone
+handle computes, so a request's result is bitwise the same alone and in the mix.
 
 Latency = completion time - arrival time; the report gives p50 / p99 and the aggregate
 space-time DoF/s over the makespan.
@@ -87,8 +90,14 @@ class Server:
     checksum, solution) may be replaced (the scheduler is tested on the CPU with fakes)."""
 
     def __init__(self, workers=4, mem_budget=None, precond=stmg.STMG_FP32, keep_solutions=False,
-                 footprint_fn=None, solve_fn=None, make_stream=None):
+                 footprint_fn=None, solve_fn=None, make_stream=None, batch=True, batch_max_bytes=2 << 30):
         self.workers = workers
+        # batching: groups of `workers` slots for shapes whose footprint is at most batch_max_bytes
+        # (a group holds the hierarchies of all its slots; large requests are bandwidth-bound anyway)
+        self.batch = batch and workers > 1
+        self.batch_max = batch_max_bytes
+        self.groups = {}                         # shape -> [Group, attached solvers]
+        self.batch_done = {"rounds": 0, "slot_vcycles": 0, "launches": 0}   # of closed groups
         self.precond = precond
         if mem_budget is None:
             import torch
@@ -105,18 +114,51 @@ class Server:
         self.keys = [None] * workers             # its shape
 
     # ---------------------------------------------------------------- worker side
+    def _release(self, w):
+        """Close worker w's resident handle (detaching it from its group; a group without
+        handles is destroyed)."""
+        if self.handles[w] is None:
+            return
+        key, S = self.handles[w]
+        with self.lock:
+            ent = self.groups.get(key)
+            if ent is not None and S in ent[1]:
+                ent[0].detach(S)
+                ent[1].remove(S)
+                if not ent[1]:
+                    for k2, v in ent[0].stats().items():
+                        self.batch_done[k2] += v
+                    ent[0].close()
+                    del self.groups[key]
+        S.close()
+        self.handles[w] = None
+
     def _handle(self, w, req, stream):
         if self.handles[w] is not None and self.handles[w][0] == req.shape:
             S = self.handles[w][1]
             S.set_physics(1.0 / req.re, req.tau, req.problem)
             return S
-        if self.handles[w] is not None:
-            self.handles[w][1].close()
-            self.handles[w] = None
-        S = stmg.Solver(request_params(req, self.precond), inputs.vertices(req.d, req.n, req.amp, req.seed),
-                        stream=stream)
+        self._release(w)
+        prm = request_params(req, self.precond)
+        verts = inputs.vertices(req.d, req.n, req.amp, req.seed)
+        S = stmg.Solver(prm, verts, stream=stream)
+        if self.batch and stmg.footprint(prm) <= self.batch_max:
+            with self.lock:
+                ent = self.groups.get(req.shape)
+                if ent is None:
+                    ent = self.groups[req.shape] = [stmg.Group(prm, verts, slots=self.workers), []]
+                ent[0].attach(S)
+                ent[1].append(S)
         self.handles[w] = (req.shape, S)
         return S
+
+    def batch_stats(self):
+        """Batched V-cycle rounds, slot V-cycles and launches over the groups alive now."""
+        tot = dict(self.batch_done)
+        for g, _ in self.groups.values():
+            for key, v in g.stats().items():
+                tot[key] += v
+        return tot
 
     def _solve(self, w, req, stream):
         import torch
@@ -136,9 +178,8 @@ class Server:
         return rc, L["Nst"], st, chk, sol
 
     def close(self):
-        for h in self.handles:
-            if h is not None:
-                h[1].close()
+        for w in range(self.workers):
+            self._release(w)
         self.handles = [None] * self.workers
 
     # ---------------------------------------------------------------- scheduler
@@ -157,9 +198,7 @@ class Server:
 
     def _evict_idle(self, free):
         for v in free:
-            if self.handles[v] is not None:
-                self.handles[v][1].close()
-                self.handles[v] = None
+            self._release(v)
             self.resident[v] = 0
             self.keys[v] = None
 

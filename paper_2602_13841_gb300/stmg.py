@@ -109,6 +109,12 @@ def load():
         "stmg_launch_count": (ctypes.c_longlong, []),
         "stmg_footprint": (I, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_uint64)]),
         "stmg_set_physics": (I, [P, D, D, I]),
+        "stmg_group_create": (I, [ctypes.POINTER(Params), P, I, P, ctypes.POINTER(P)]),
+        "stmg_group_destroy": (None, [P]),
+        "stmg_group_attach": (I, [P, P]),
+        "stmg_group_detach": (I, [P, P]),
+        "stmg_group_stats": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(ctypes.c_longlong)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -314,3 +320,55 @@ class Solver:
         if check:
             self._check(rc, "slab_solve")
         return rc, st.as_dict()
+
+
+class Group:
+    """Batched preconditioning for handles of one shape (stmg_group_*): attached Solvers share one
+    hierarchy with `slots` slots and their V-cycles run as batched launches.  Their slab solves must
+    run on different host threads."""
+
+    def __init__(self, params, vertices=None, slots=4, stream=None):
+        import torch
+        self.lib = load()
+        self.params = params
+        if stream is None:
+            stream = torch.cuda.Stream().cuda_stream
+        self.stream = stream
+        vp = None
+        if vertices is not None:
+            self._verts = np.ascontiguousarray(vertices, dtype=np.float64)
+            vp = self._verts.ctypes.data_as(ctypes.c_void_p)
+        g = ctypes.c_void_p()
+        st = self.lib.stmg_group_create(ctypes.byref(params), vp, int(slots), ctypes.c_void_p(stream), ctypes.byref(g))
+        if st != 0:
+            raise StmgError(st, "stmg_group_create failed")
+        self.g = g
+        self.members = []
+
+    def attach(self, solver):
+        st = self.lib.stmg_group_attach(self.g, solver.h)
+        if st != 0:
+            raise StmgError(st, "group_attach: %s" % self.lib.stmg_last_error(solver.h).decode())
+        self.members.append(solver)
+
+    def detach(self, solver):
+        if solver in self.members:
+            self.lib.stmg_group_detach(self.g, solver.h)
+            self.members.remove(solver)
+
+    def stats(self):
+        r, v, l = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        self.lib.stmg_group_stats(self.g, ctypes.byref(r), ctypes.byref(v), ctypes.byref(l))
+        return {"rounds": r.value, "slot_vcycles": v.value, "launches": l.value}
+
+    def close(self):
+        if getattr(self, "g", None):
+            self.lib.stmg_group_destroy(self.g)
+            self.g = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
