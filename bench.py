@@ -23,6 +23,7 @@ sample of the same workload on the host cores.  With torchrun, every rank runs a
 replica (the slab solve does not shard); rank 0 prints the JSON line.
 """
 import argparse
+import faulthandler
 import json
 import os
 import subprocess
@@ -281,6 +282,8 @@ def run_reference(args):
 
 
 def main():
+    # a crash in native code prints the Python stack of every thread
+    faulthandler.enable(all_threads=True)
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=4)

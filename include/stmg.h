@@ -292,14 +292,16 @@ stmg_status stmg_slab_solve(stmg_handle* h, double t_start, const double* V_prev
  * arrived.  Each slot computes exactly what a handle without a group computes, so results are
  * bitwise the same alone and in a batch.  Slab solves of attached handles must run on different
  * host threads (they wait for each other); stmg_smoother_sweep / stmg_vcycle / stmg_transfer /
- * stmg_level_state are not available on attached handles (STMG_ERR_ARG).  The group runs on its
- * own stream (`stream`), ordered against the handles' streams by events.  Device memory: the
- * hierarchy of `slots` handles (an attached handle allocates no hierarchy of its own). */
+ * stmg_level_state are not available on attached handles (STMG_ERR_ARG).  The group runs on a
+ * non-blocking stream that it creates and owns (a stream shared with any other user could be
+ * touched by another thread while a V-cycle graph is being captured on it), ordered against the
+ * handles' streams by events.  Device memory: the hierarchy of `slots` handles (an attached
+ * handle allocates no hierarchy of its own). */
 typedef struct stmg_group stmg_group;
 
-/* Create a group for handles shaped like p / vertices (as stmg_create), 1 <= slots <= 16. */
-stmg_status stmg_group_create(const stmg_params* p, const double* vertices, int slots, stmg_stream stream,
-                              stmg_group** out);
+/* Create a group for handles shaped like p / vertices (as stmg_create), 1 <= slots <= 16, on the
+ * current device.  *out is NULL on any error. */
+stmg_status stmg_group_create(const stmg_params* p, const double* vertices, int slots, stmg_group** out);
 /* Destroy a group; attached handles are detached first (their next solve allocates their own
  * hierarchy).  No solve of an attached handle may be running. */
 void stmg_group_destroy(stmg_group* g);

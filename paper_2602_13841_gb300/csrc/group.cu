@@ -6,8 +6,9 @@
 // once for all ready slots (blockIdx.y / z = slot) -- has produced its correction.  A round starts
 // when every handle inside a slab solve is ready, or after a short wait for the stragglers.  Slot j
 // computes exactly what a lone handle computes (same kernels, per-slot data only), so a solve
-// gives the same bits alone and in a batch.  All group work runs on the group's stream; the
-// handles' streams are ordered against it with events.
+// gives the same bits alone and in a batch.  All group work runs on the group's own stream
+// (created here: a stream that another thread may use must never be the one a V-cycle graph is
+// being captured on); the handles' streams are ordered against it with events.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -28,6 +29,7 @@ namespace stmg {
 
 struct Group {
   Handle* core = nullptr;           // levels of the shape and the B-slot hierarchy (group stream)
+  cudaStream_t stream = nullptr;    // owned by the group
   int B = 1;
   std::mutex m;
   std::condition_variable cv;
@@ -47,6 +49,7 @@ struct Group {
     for (auto e : ev_in) if (e) cudaEventDestroy(e);
     if (ev_done) cudaEventDestroy(ev_done);
     if (core) stmg_destroy(reinterpret_cast<stmg_handle*>(core));
+    if (stream) cudaStreamDestroy(stream);
   }
 };
 
@@ -173,13 +176,17 @@ using namespace stmg;
 
 extern "C" {
 
-stmg_status stmg_group_create(const stmg_params* p, const double* vertices, int slots, stmg_stream stream,
-                              stmg_group** out) {
+stmg_status stmg_group_create(const stmg_params* p, const double* vertices, int slots, stmg_group** out) {
   if (!p || !out || slots < 1 || slots > 16) return STMG_ERR_ARG;
   *out = nullptr;
   auto g = std::make_unique<Group>();
+  if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    g->stream = nullptr;
+    cudaGetLastError();
+    return STMG_ERR_CUDA;
+  }
   stmg_handle* hh = nullptr;
-  stmg_status st = stmg_create(p, vertices, stream, &hh);
+  stmg_status st = stmg_create(p, vertices, reinterpret_cast<stmg_stream>(g->stream), &hh);
   if (st != STMG_OK) return st;
   g->core = reinterpret_cast<Handle*>(hh);
   g->B = slots;

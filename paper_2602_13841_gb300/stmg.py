@@ -109,7 +109,7 @@ def load():
         "stmg_launch_count": (ctypes.c_longlong, []),
         "stmg_footprint": (I, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_uint64)]),
         "stmg_set_physics": (I, [P, D, D, I]),
-        "stmg_group_create": (I, [ctypes.POINTER(Params), P, I, P, ctypes.POINTER(P)]),
+        "stmg_group_create": (I, [ctypes.POINTER(Params), P, I, ctypes.POINTER(P)]),
         "stmg_group_destroy": (None, [P]),
         "stmg_group_attach": (I, [P, P]),
         "stmg_group_detach": (I, [P, P]),
@@ -327,19 +327,15 @@ class Group:
     hierarchy with `slots` slots and their V-cycles run as batched launches.  Their slab solves must
     run on different host threads."""
 
-    def __init__(self, params, vertices=None, slots=4, stream=None):
-        import torch
+    def __init__(self, params, vertices=None, slots=4):
         self.lib = load()
         self.params = params
-        if stream is None:
-            stream = torch.cuda.Stream().cuda_stream
-        self.stream = stream
         vp = None
         if vertices is not None:
             self._verts = np.ascontiguousarray(vertices, dtype=np.float64)
             vp = self._verts.ctypes.data_as(ctypes.c_void_p)
         g = ctypes.c_void_p()
-        st = self.lib.stmg_group_create(ctypes.byref(params), vp, int(slots), ctypes.c_void_p(stream), ctypes.byref(g))
+        st = self.lib.stmg_group_create(ctypes.byref(params), vp, int(slots), ctypes.byref(g))
         if st != 0:
             raise StmgError(st, "stmg_group_create failed")
         self.g = g
