@@ -43,7 +43,7 @@ typedef enum {
   STMG_ERR_ARG = 1,           /* invalid argument or unsupported size */
   STMG_ERR_OOM = 2,           /* device allocation failed */
   STMG_ERR_CUDA = 3,          /* a CUDA call failed */
-  STMG_ERR_NOT_CONVERGED = 4, /* Newton reached its iteration cap */
+  STMG_ERR_NOT_CONVERGED = 4, /* Newton reached its iteration cap (or stalled, newton_stall_steps) */
   STMG_ERR_NUMERIC = 5,       /* NaN / Inf detected */
   STMG_ERR_TIMEOUT = 6,       /* a bounded device wait ran out */
   STMG_ERR_UNSUPPORTED = 7    /* configuration not compiled in */
@@ -113,6 +113,11 @@ typedef struct {
                           lower time degree (the DG(k) levels of the paper's p-coarsening), in place
                           of nu1 / nu2 there; <= 0 (default): nu1 / nu2 on every level.  The temporal
                           modes that DG(k) -> DG(k/2) drops are left to the smoother of those levels */
+  int newton_stall_steps;    /* > 0: stop with STMG_ERR_NOT_CONVERGED once ||R||_M after a Newton step
+                                exceeds newton_stall_ratio times its value newton_stall_steps steps
+                                earlier (a solve that makes no progress releases the GPU early;
+                                a serving policy, not part of Alg. 1).  <= 0 (default): off */
+  double newton_stall_ratio; /* e.g. 0.9 */
 } stmg_params;
 
 /* Fill *p with the paper's defaults (Sec. 5, Alg. 1-2) for a d-dimensional problem. */

@@ -289,8 +289,10 @@ static stmg_status newton(Handle* h, MG<T>& mg, double t0, const double* Vprev, 
   double nprev = n0, eta = P.ew_eta0, rho_prev = 1.0;
   int kap_prev = 1, kap_ref = 1;
   std::vector<double> window{0.5 * n0 * n0};
+  std::vector<double> hist{n0};                   // ||R||_M after every step (stall check)
+  bool stalled = false;
   int k = 0;
-  while (nr > std::max(P.newton_atol, P.newton_rtol * n0) && k < P.newton_maxit) {
+  while (nr > std::max(P.newton_atol, P.newton_rtol * n0) && k < P.newton_maxit && !stalled) {
     if (rho_prev >= P.rebuild_thetaN || kap_prev >= std::max(P.rebuild_thetaL * kap_ref, (double)P.rebuild_kappa_abs)) {
       CKS(rebuild<T>(h, mg, X, st));
       kap_ref = std::max(1, kap_prev);
@@ -357,12 +359,16 @@ static stmg_status newton(Handle* h, MG<T>& mg, double t0, const double* Vprev, 
       if (stag) CKS(rebuild<T>(h, mg, X, st));
     }
     ++k;
+    hist.push_back(nr);
+    const int ss = P.newton_stall_steps;
+    if (ss > 0 && (int)hist.size() > ss && nr > P.newton_stall_ratio * hist[hist.size() - 1 - ss]) stalled = true;
   }
   st->newton_its = k;
   st->res_final = nr;
 #undef CKS
   if (nr > std::max(P.newton_atol, P.newton_rtol * n0))
-    return h->fail(STMG_ERR_NOT_CONVERGED, "slab_solve: Newton reached its iteration cap");
+    return h->fail(STMG_ERR_NOT_CONVERGED, stalled ? "slab_solve: Newton stalled (no progress over newton_stall_steps steps)"
+                                                   : "slab_solve: Newton reached its iteration cap");
   return STMG_OK;
 }
 

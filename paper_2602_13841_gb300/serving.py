@@ -10,7 +10,9 @@ shape (d, n, r, k) reuses the hierarchy and work space (stmg_set_physics), and a
 that holds the request's shape is preferred.  The solves of different workers overlap on the
 device.  With batching on (default), the handles of one shape held by different workers attach
 to a shared group (stmg_group_*): while several requests of that shape are being solved, their
-V-cycles run as batched launches (one launch per kernel for all of them).  All kernels are
+V-cycles run as batched launches (one launch per kernel for all of them); a waiting request
+whose shape is being solved is admitted ahead of the others among the first few in line, so
+that same-shape requests meet.  All kernels are
 deterministic (fixed reduction order, coloured scatter) and a batched slot computes what a lone
 handle computes, so a request's result is bitwise the same alone and in the mix.
 
@@ -80,9 +82,12 @@ def poisson_stream(n_requests, rate, seed, shapes2d=(16, 32, 64, 128, 256), shap
 
 
 def request_params(req, precond=stmg.STMG_FP32):
+    """Solver parameters of a request: Newton to 1e-10 relative; a solve whose residual drops by
+    less than 10 % over three Newton steps stops early (STMG_ERR_NOT_CONVERGED) and frees its
+    worker."""
     return stmg.default_params(dim=req.d, n_cells_1d=req.n, r=req.r, k=req.k, nu=1.0 / req.re, tau=req.tau,
                                problem=req.problem, precond_precision=precond, newton_rtol=1e-10,
-                               newton_atol=1e-14)
+                               newton_atol=1e-14, newton_stall_steps=3, newton_stall_ratio=0.9)
 
 
 class Server:
@@ -90,12 +95,14 @@ class Server:
     checksum, solution) may be replaced (the scheduler is tested on the CPU with fakes)."""
 
     def __init__(self, workers=4, mem_budget=None, precond=stmg.STMG_FP32, keep_solutions=False,
-                 footprint_fn=None, solve_fn=None, make_stream=None, batch=True, batch_max_bytes=2 << 30):
+                 footprint_fn=None, solve_fn=None, make_stream=None, batch=True, batch_max_bytes=2 << 30,
+                 batch_window=8):
         self.workers = workers
         # batching: groups of `workers` slots for shapes whose footprint is at most batch_max_bytes
         # (a group holds the hierarchies of all its slots; large requests are bandwidth-bound anyway)
         self.batch = batch and workers > 1
         self.batch_max = batch_max_bytes
+        self.batch_window = batch_window
         self.groups = {}                         # shape -> [Group, attached solvers]
         self.batch_done = {"rounds": 0, "slot_vcycles": 0, "launches": 0}   # of closed groups
         self.precond = precond
@@ -196,6 +203,18 @@ class Server:
                     best = w                     # replace the largest resident handle first
         return best
 
+    def _admission_order(self, waiting, free):
+        """Indices of `waiting` in the order they are offered a worker: arrival order, except that
+        with batching on, a request among the first `batch_window` whose shape is being solved
+        right now goes first (it joins that solve's group, so their V-cycles share launches)."""
+        order = list(range(len(waiting)))
+        if not (self.batch and free and self.batch_window > 0):
+            return order
+        busy = {self.keys[v] for v in range(self.workers) if v not in free and self.keys[v] is not None}
+        head = [i for i in order[:self.batch_window]
+                if waiting[i][0].shape in busy and waiting[i][1] <= self.batch_max]
+        return head + [i for i in order if i not in head]
+
     def _evict_idle(self, free):
         for v in free:
             self._release(v)
@@ -237,7 +256,8 @@ class Server:
                     q = pending.popleft()
                     waiting.append((q, self.footprint_fn(q)))
                 progressed = False
-                for i, (q, fp) in enumerate(waiting):
+                for i in self._admission_order(waiting, free):
+                    q, fp = waiting[i]
                     if fp > self.mem_budget:                 # can never run: reject
                         results[q.rid] = Result(q.rid, 2, 0, q.arrival, t, t, 0, 0, float("nan"))
                         waiting.pop(i)

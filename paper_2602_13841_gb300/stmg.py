@@ -57,6 +57,7 @@ class Params(ctypes.Structure):
         ("stag_s", ctypes.c_int), ("stag_theta", ctypes.c_double),
         ("omega_p", ctypes.c_double), ("vanka_fp16", ctypes.c_int), ("build_chunk_cells", ctypes.c_int),
         ("keep_time_degree", ctypes.c_int), ("smoother", ctypes.c_int), ("nu_tc", ctypes.c_int),
+        ("newton_stall_steps", ctypes.c_int), ("newton_stall_ratio", ctypes.c_double),
     ]
 
 

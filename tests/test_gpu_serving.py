@@ -30,3 +30,34 @@ def test_mixed_stream_results_equal_solo_results():
         solo.close()
         assert s.status == 0
         assert np.array_equal(s.solution, r.solution), q
+
+
+def test_newton_stall_stop():
+    """A solve that makes no progress (2D 32^2 Q2/P1 DG(0) Taylor-Green at Re 1623: the two-grid
+    iteration diverges there) stops after newton_stall_steps steps with STMG_ERR_NOT_CONVERGED; a
+    converging solve is unchanged by the setting."""
+    import torch
+    from paper_2602_13841_gb300 import inputs, stmg
+    build_and_load()
+
+    def solve(k, stall):
+        p = stmg.default_params(dim=2, n_cells_1d=32, r=1, k=k, nu=1.0 / 1623, tau=0.05, problem="TG2D",
+                                newton_rtol=1e-10, newton_atol=1e-14, newton_stall_steps=stall,
+                                newton_stall_ratio=0.9)
+        S = stmg.Solver(p, inputs.vertices(2, 32, 0.1, 1))
+        L = S.levels[0]
+        V0 = torch.empty(L["Nv"], dtype=torch.float64, device="cuda")
+        U = torch.empty(L["Nst"], dtype=torch.float64, device="cuda")
+        S.initial_condition(V0)
+        S.initial_guess(V0, U)
+        rc, st = S.slab_solve(0.0, V0, U, check=False)
+        msg = S.lib.stmg_last_error(S.h).decode()
+        S.close()
+        return rc, st, msg
+
+    rc, st, msg = solve(0, 3)
+    assert rc == 4 and st["newton_its"] == 3 and "stalled" in msg    # STMG_ERR_NOT_CONVERGED
+    assert st["res_final"] > 0.9 * st["res0"]
+    rc0, st0, _ = solve(1, 0)
+    rc1, st1, _ = solve(1, 3)
+    assert rc0 == rc1 == 0 and st0["newton_its"] == st1["newton_its"] and st0["res_final"] == st1["res_final"]

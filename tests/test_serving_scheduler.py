@@ -63,3 +63,24 @@ def test_resident_shape_is_reused():
     S.run(_reqs([(16, 0.0)]), realtime=False)
     w16 = [w for w, s in calls if s[1] == 16]
     assert w16[0] == w16[1]                        # the worker holding the shape took it again
+
+
+def test_batching_admits_a_request_of_a_running_shape_first():
+    def run(batch):
+        order = []
+
+        def solve(w, q, stream):
+            order.append(q.rid)
+            time.sleep(0.05)
+            return 0, 1, {}, 0.0, None
+
+        S = Server(workers=2, mem_budget=1000, footprint_fn=lambda q: 10, solve_fn=solve,
+                   make_stream=lambda: None, batch=batch)
+        # request 0 and 3 share a shape (n = 8); 1 and 2 are of other shapes
+        S.run(_reqs([(8, 0.0), (16, 0.0), (24, 0.0), (8, 0.0)]), realtime=False)
+        return order
+
+    fifo = run(False)
+    assert fifo.index(1) < fifo.index(3)
+    batched = run(True)
+    assert batched[:2] == [0, 3]                   # request 3 joins request 0's shape at once
