@@ -607,10 +607,47 @@ def operator_apply(S, U, stream, dev, w, args, peaks, reps=25, warm=5):
         hbm = peaks.get("hbm_gbs", 6800.0)
         out[name] = {"gdof_s": Nst / t / 1e9, "median_ms": t * 1e3, "launches_timed": reps,
                      "algorithmic_bytes": byt, "achieved_gbs": byt / t / 1e9, "hbm_frac": byt / t / 1e9 / hbm}
+    # the same FP32 apply on the first coarser level (Q2/P1, DG(1) for the 2D headline hierarchy),
+    # at a seeded state (the apply's cost does not depend on the values)
+    if len(S.levels) > 1:
+        L1 = S.levels[1]
+        n1 = L1["Nst"]
+        with torch.cuda.stream(stream):
+            Us1 = torch.tensor(inputs.uniform(n1, 43), dtype=torch.float32, device=dev)
+            x1 = torch.tensor(inputs.uniform(n1, 44), dtype=torch.float32, device=dev)
+            y1 = torch.empty_like(x1)
+            for _ in range(warm):
+                S.apply(Us1, x1, y1, level=1, precision=stmg.STMG_FP32)
+            times = []
+            for _ in range(reps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                S.apply(Us1, x1, y1, level=1, precision=stmg.STMG_FP32)
+                b.record(stream)
+                b.synchronize()
+                times.append(a.elapsed_time(b))
+        t1 = float(np.median(times)) * 1e-3
+        byt1 = 4 * (L1["k"] + 1) * (3 * L1["Nv"] + 2 * L1["Np"]) + 8 * w["d"] * (w["n"] + 1) ** w["d"]
+        out["fp32_level1"] = {"level": "r=%d k=%d" % (L1["r"], L1["k"]), "gdof_s": n1 / t1 / 1e9,
+                              "median_ms": t1 * 1e3, "algorithmic_bytes": byt1, "achieved_gbs": byt1 / t1 / 1e9,
+                              "hbm_frac": byt1 / t1 / 1e9 / peaks.get("hbm_gbs", 6800.0)}
+    # FP32 compute roofline of the finest-level apply (2D Q3/P2/DG(2)): FP32 operations per cell
+    # and time node, counted by ncu on one 256^2 launch (FFMA x 2 + FMUL + FADD, the tile's halo
+    # recompute taken out), against the FP32 FMA peak of 152 SMs at 2.07 GHz
+    if w["d"] == 2 and w["r"] == 2 and w["k"] == 2 and "fp32" in out:
+        flops = FP32_APPLY_FLOPS_PER_CELL_NODE * (w["k"] + 1) * w["n"] ** 2
+        t32 = out["fp32"]["median_ms"] * 1e-3
+        out["fp32"]["alu_roofline"] = {
+            "bound": "alu", "flops": flops, "achieved_tflops": flops / t32 / 1e12, "peak_tflops": FP32_PEAK_TFLOPS,
+            "frac": flops / t32 / 1e12 / FP32_PEAK_TFLOPS,
+            "hbm_frac_at_alu_peak": (out["fp32"]["algorithmic_bytes"] / (peaks.get("hbm_gbs", 6800.0) * 1e9))
+                                    / (flops / (FP32_PEAK_TFLOPS * 1e12))}
     out["note"] = ("FP64 (colour-split warp kernel): bound by the DFMA pipe (84 % pipe utilisation in the ncu "
                    "capture), so its HBM fraction is low by construction; FP32 (tiled single-launch kernel): "
-                   "bound by FP32 instruction issue (its FFMA/FMUL/FADD count alone is about 22 M warp "
-                   "instructions per apply at 256^2), so the HBM fraction is capped well below the copy peak")
+                   "its FP32 operations take longer at the FP32 peak than its bytes take at the HBM peak "
+                   "(alu_roofline.hbm_frac_at_alu_peak is the HBM fraction that operation count allows), and it "
+                   "runs at alu_roofline.frac of the FP32 peak, bound by instruction issue")
     return out
 
 
@@ -636,10 +673,19 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
-# DRAM bytes (read + write) per cell of the finest-level Vanka apply, FP32 inverses, Q3/P2/DG(2):
-# ncu capture of one colour launch on the 192^2 mesh of the same recipe, 180.53 MB for 9216
-# cells; scaled to a 256^2 launch by its cells.
-VANKA_DRAM_BYTES_PER_CELL = 180.529664e6 / 9216
+# FP32 operations per cell and time node of the 2D Q3/P2/DG(2) FP32 Jacobian apply
+# (k_apply2d_tile<float, 4, 3>): ncu on one 256^2 launch executed 16.80 M FFMA and 6.08 M other FP32
+# warp instructions, i.e. 32 (2 x 16.80 + 6.08) M = 1.270 GFLOP, of which the tile's halo
+# recompute is 22 % (16 x 8 cells computed per 15 x 7 owned): 1.270e9 / 1.219 / (3 x 65536).
+FP32_APPLY_FLOPS_PER_CELL_NODE = 1.270e9 / (128.0 / 105.0) / (3 * 65536)
+# FP32 FMA peak of one GB300: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz / 1e12 (about 120 FFMA per
+# SM per clock sustained in a dependent-chain probe, 73.4 TFLOP/s).
+FP32_PEAK_TFLOPS = 73.4
+
+# DRAM bytes (read + write) per cell of the finest-level Vanka apply (k_vanka_apply_ws), FP32
+# inverses, Q3/P2/DG(2): ncu capture of one colour launch on the 128^2 mesh of the same recipe,
+# 78.69 MB for 4096 cells; scaled to a 256^2 launch by its cells.
+VANKA_DRAM_BYTES_PER_CELL = 78.690304e6 / 4096
 
 
 def _inverse_gb(w, args):
@@ -664,13 +710,13 @@ def roofline(S, prof, args):
     d = WORKLOADS[args.workload]["d"]
     cells = (args.n // 2) ** d                     # cells of one colour launch on the finest level
     traffic = VANKA_DRAM_BYTES_PER_CELL * cells if (args.vanka_fp16 == 0 and args.workload == "2d") else None
-    name = ("finest-level Vanka patch apply (k_vanka_apply; k_vanka_apply_global where the patch "
-            "exceeds shared memory)")
+    name = ("finest-level Vanka patch apply (k_vanka_apply_ws for the 2D levels; k_vanka_apply / "
+            "k_vanka_apply_global in 3D)")
     return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
             "algorithmic_bytes_per_launch": k["bytes"] / k["count"],
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-            "traffic_source": "ncu 192^2 capture scaled by cells per launch" if traffic else None,
+            "traffic_source": "ncu 128^2 capture scaled by cells per launch" if traffic else None,
             "launches": k["count"], "avg_us": 1e3 * k["ms"] / k["count"]}
 
 

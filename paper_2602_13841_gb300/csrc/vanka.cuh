@@ -671,6 +671,13 @@ template <> struct InvLd<__half> {
   __device__ static float2 cx(const __half* p) { return __half22float2(*reinterpret_cast<const __half2*>(p)); }
 };
 
+// Rows of the spatial Vanka patch of Q_{N-1} / P_{N-2}^disc: D N^D velocity DoFs and C(r+D, D)
+// pressure modes (r = N - 2), known at compile time so that the row products unroll.
+template <int D, int N>
+__host__ __device__ constexpr int patch_rows() {
+  return D * Shape<D, N>::Q + (D == 2 ? (N - 1) * N / 2 : (N - 1) * N * (N + 1) / 6);
+}
+
 // Dynamic shared memory of k_vanka_apply: [blob | rt (kp1 x mr T) | gb (ms int64) | mbarrier].
 __host__ __device__ inline size_t apply_blob_bytes(int kp1, int ms, size_t si) {
   return ((size_t)kp1 * ms * inv_stride(ms, (int)si) * si + 127) & ~(size_t)127;
@@ -808,6 +815,218 @@ __global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const 
     for (int e = 0; e < MAXKP1; ++e)
       if (e < te.nblk) y += te.Gre[a][e] * yr[e] - te.Gim[a][e] * yi[e];
     d[g + a * sa] = dold[a] + wgt * y;
+  }
+}
+
+// Warp-specialised persistent form of k_vanka_apply for patches whose inverse is small (the 2D
+// levels).  A block owns a ring of S stages in shared memory and walks the cells cidx =
+// blockIdx.x + t gridDim.x (t = 0, 1, ...) of the colour.  Warp 0 produces: one lane streams the
+// inverse of cell t into stage t % S by bulk copies (the stage's full barrier) as soon as the
+// cell that used the stage before has been solved (its empty barrier).  C consumer groups of TPC
+// threads solve the cells t = g, g + C, ...: thread i of a group owns row i, gathers the residual
+// and correction of the group's next cell into registers before it waits for the current
+// inverse, and the group releases the stage when it is done.  Copies thus stay in flight while
+// cells are solved and C cells are solved at once, instead of every block waiting for its own
+// copy, solving and ending.  Cells of one colour have disjoint patches, so a correction gathered
+// ahead is still current when its cell is solved.  The products are those of k_vanka_apply, in
+// the same order.
+// Shared memory: [S stages | C rt buffers (kp1 x mr T) | full[S] | empty[S] | abort flag].
+__host__ __device__ inline size_t ws_rt_bytes(int kp1, int ms, size_t t) {
+  return ((size_t)kp1 * ((ms + 1) & ~1) * t + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t ws_smem_bytes(int kp1, int ms, size_t si, size_t t, int S, int C) {
+  return (size_t)S * apply_blob_bytes(kp1, ms, si) + (size_t)C * ws_rt_bytes(kp1, ms, t) + (size_t)2 * S * 8 + 16;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Named barrier `id` over n threads that also returns whether v held in all of them.
+__device__ __forceinline__ bool group_and(int id, int n, bool v) {
+  uint32_t r;
+  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+               : "=r"(r) : "r"((uint32_t)v), "r"(id), "r"(n) : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void group_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Global index of patch row l of the cell at cc (velocity: component-major nodes; pressure: the
+// cell's modes after the (k+1) velocity blocks) and the stride between its time nodes.
+template <typename T, int D, int N>
+__device__ __forceinline__ int64_t patch_row_index(const LevelArgs<T>& L, const int* cc, int64_t cell, int l,
+                                                   int kp1, int npc, int64_t* sa) {
+  constexpr int NL = Shape<D, N>::Q;
+  constexpr int MV = D * NL;
+  if (l < MV) {
+    *sa = L.Nv;
+    return (l / NL) * L.nnodes + global_node<D>(L.N1, cc, N - 1, l % NL, N);
+  }
+  *sa = L.Np;
+  return (int64_t)kp1 * L.Nv + cell * npc + (l - MV);
+}
+
+template <typename T, typename SI, int D, int N>
+__global__ void k_vanka_apply_ws(LevelArgs<T> L, const SI* __restrict__ inv, const float* __restrict__ scale,
+                                 const T* __restrict__ res, T* __restrict__ d, T omega, T omega_p, int kp1, int npc,
+                                 TEig<T> te, ColorInfo ci, int* __restrict__ wstat, unsigned extra_tx,
+                                 SlotStrides zs, int S, int C, int TPC) {
+  inv += blockIdx.y * zs.inv;
+  if (scale) scale += blockIdx.y * zs.scale;
+  res += blockIdx.y * zs.vec;
+  d += blockIdx.y * zs.vec;
+  constexpr int NL = Shape<D, N>::Q;
+  constexpr int MV = D * NL;
+  const int ms = MV + npc, st = inv_stride(ms, (int)sizeof(SI)), mr = (ms + 1) & ~1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const size_t blob = apply_blob_bytes(kp1, ms, sizeof(SI));
+  const size_t rtb = ws_rt_bytes(kp1, ms, sizeof(T));
+  unsigned char* rt_base = smem_raw + (size_t)S * blob;
+  uint64_t* full = reinterpret_cast<uint64_t*>(rt_base + (size_t)C * rtb);
+  uint64_t* empty = full + S;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
+  const int tid = threadIdx.x;
+  const int G = (int)gridDim.x;
+  const int ncell = ci.count > (int)blockIdx.x ? (ci.count - (int)blockIdx.x + G - 1) / G : 0;
+  if (ncell == 0) return;                                                             // block-uniform
+  const uint32_t bytes = (uint32_t)((size_t)kp1 * ms * st * sizeof(SI));
+  auto cell_of = [&](int t, int* cc) -> int64_t {
+    decode_color_cell<D>(ci, (int)blockIdx.x + t * G, cc);
+    int64_t c = 0, m = 1;
+    for (int l = 0; l < D; ++l) { c += (int64_t)cc[l] * m; m *= L.n; }
+    return c;
+  };
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_addr(full + s), 1);
+      mbar_init(smem_addr(empty + s), 1);
+    }
+    *abort_flag = 0;
+  }
+  __syncthreads();                                   // barriers initialised
+  int issued = 0;                                    // producer lane: cells whose copies were issued
+  if (tid < 32) {
+    if (tid == 0) {
+      for (int t = 0; t < ncell; ++t) {
+        if (*abort_flag) break;
+        const int s = t % S;
+        if (t >= S) {
+          // cell t - S has been solved: the stage is free
+          if (!mbar_wait_bounded(smem_addr(empty + s), (uint32_t)(((t / S) - 1) & 1), kWaitLimit)) {
+            atomicExch(wstat, 1);
+            *abort_flag = 1;
+            break;
+          }
+          // order the consumers' generic reads of the stage before the async-proxy writes
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        int cc[3] = {0, 0, 0};
+        const int64_t c = cell_of(t, cc);
+        const uint32_t b = smem_addr(full + s);
+        mbar_expect_tx(b, bytes + (t == 0 ? extra_tx : 0u));   // extra_tx > 0 only under the failure-test hook
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(inv + c * (int64_t)kp1 * ms * st);
+        unsigned char* dst = smem_raw + (size_t)s * blob;
+        for (uint32_t o = 0; o < bytes; o += kBulkChunk) {
+          const uint32_t n = bytes - o < (uint32_t)kBulkChunk ? bytes - o : (uint32_t)kBulkChunk;
+          bulk_g2s(smem_addr(dst + o), src + o, n, b);
+        }
+        issued = t + 1;
+      }
+    }
+  } else if ((tid - 32) / TPC < C) {
+    const int g = (tid - 32) / TPC, i = (tid - 32) % TPC;
+    T* rt = reinterpret_cast<T*>(rt_base + (size_t)g * rtb);
+    const bool row = i < ms;
+    int64_t gi = 0, sa = 0, cell = 0;
+    T ra[MAXKP1] = {}, dold[MAXKP1] = {};
+    // row i of cell t: global index, residual and old correction (registers)
+    auto gather = [&](int t) {
+      int cc[3] = {0, 0, 0};
+      cell = cell_of(t, cc);
+      if (!row) return;
+      gi = patch_row_index<T, D, N>(L, cc, cell, i, kp1, npc, &sa);
+#pragma unroll
+      for (int a = 0; a < MAXKP1; ++a) {
+        ra[a] = a < kp1 ? res[gi + a * sa] : (T)0;
+        dold[a] = a < kp1 ? d[gi + a * sa] : (T)0;
+      }
+    };
+    if (g < ncell) gather(g);
+    for (int t = g; t < ncell; t += C) {
+      const int s = t % S;
+      // the time-eigenbasis transform of this cell's residual
+      if (row) {
+        for (int e = 0; e < te.nblk; ++e) {
+          T fr = 0, fi = 0;
+#pragma unroll
+          for (int a = 0; a < MAXKP1; ++a) { fr += te.Fre[e][a] * ra[a]; fi += te.Fim[e][a] * ra[a]; }
+          rt[te.off[e] * mr + i] = fr;
+          if (te.cplx[e]) rt[(te.off[e] + 1) * mr + i] = fi;
+        }
+      }
+      const int64_t gcur = gi, scur = sa, ccur = cell;
+      T dcur[MAXKP1];
+#pragma unroll
+      for (int a = 0; a < MAXKP1; ++a) dcur[a] = dold[a];
+      // the group's next cell: its gather is in flight while this one waits and is solved
+      if (t + C < ncell) gather(t + C);
+      bool ok = mbar_wait_bounded(smem_addr(full + s), (uint32_t)((t / S) & 1), kWaitLimit);
+      ok = group_and(1 + g, TPC, ok && !*abort_flag);   // rt complete; one decision for the group
+      if (!ok) {
+        if (i == 0) { atomicExch(wstat, 1); *abort_flag = 1; }
+        break;
+      }
+      if (row) {
+        const SI* sinv = reinterpret_cast<const SI*>(smem_raw + (size_t)s * blob);
+        T yr[MAXKP1], yi[MAXKP1];
+#pragma unroll
+        for (int e = 0; e < MAXKP1; ++e) { yr[e] = 0; yi[e] = 0; }
+        for (int e = 0; e < te.nblk; ++e) {
+          const SI* blk = sinv + (int64_t)te.off[e] * ms * st;
+          const T* r0 = rt + te.off[e] * mr;
+          T ar = 0, ai = 0;
+          if (!te.cplx[e]) {
+#pragma unroll
+            for (int j = 0; j < patch_rows<D, N>(); ++j) ar += (T)InvLd<SI>::re(blk + j * st + i) * r0[j];
+          } else {
+            const T* r1 = r0 + mr;
+#pragma unroll
+            for (int j = 0; j < patch_rows<D, N>(); ++j) {
+              const auto v = InvLd<SI>::cx(blk + 2 * (j * st + i));
+              const T vr = (T)v.x, vi = (T)v.y, xr = r0[j], xi = r1[j];
+              ar += vr * xr - vi * xi;
+              ai += vr * xi + vi * xr;
+            }
+          }
+          const T sc = scale ? (T)scale[ccur * te.nblk + e] : (T)1;
+#pragma unroll
+          for (int q = 0; q < MAXKP1; ++q)
+            if (q == e) { yr[q] = sc * ar; yi[q] = sc * ai; }
+        }
+        const T wgt = i < MV ? omega : omega_p;
+#pragma unroll
+        for (int a = 0; a < MAXKP1; ++a) {
+          if (a >= kp1) break;
+          T y = 0;
+#pragma unroll
+          for (int e = 0; e < MAXKP1; ++e)
+            if (e < te.nblk) y += te.Gre[a][e] * yr[e] - te.Gim[a][e] * yi[e];
+          d[gcur + a * scur] = dcur[a] + wgt * y;
+        }
+      }
+      group_sync(1 + g, TPC);                        // the group is done with stage s and rt
+      if (i == 0) mbar_arrive(smem_addr(empty + s));
+    }
+  }
+  __syncthreads();
+  // after a failure, copies may still be in flight: wait (bounded) for the latest use of every
+  // stage before the block's shared memory is given up
+  if (tid == 0 && *abort_flag) {
+    for (int s = 0; s < S && s < issued; ++s) {
+      const int u = (issued - 1 - s) / S;            // latest use of stage s: cell s + u S
+      mbar_wait_bounded(smem_addr(full + s), (uint32_t)(u & 1), kWaitLimit);
+    }
   }
 }
 

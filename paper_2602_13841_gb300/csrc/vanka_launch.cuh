@@ -2,6 +2,8 @@
 // vanka_d3_*.cu) and the dispatch in vanka.cu: shared-memory budgets, the build of one level and
 // the colour launches of one sweep, per element type T, dimension D and N = r + 2.
 #pragma once
+#include <cstdlib>
+#include <cstring>
 #include <type_traits>
 
 #include "mg.hpp"
@@ -40,6 +42,20 @@ static size_t elem_smem_any(const Level& lv, size_t es) {
 
 // The patch matrices of a cell fit shared memory (else k_patch_global, global workspace).
 static bool patch_onchip(const Level& lv, size_t es) { return patch_smem(lv, es) <= 227 * 1024; }
+
+// Consumer groups of the warp-specialised persistent apply (k_vanka_apply_ws), which serves 2D
+// patches of more than 32 rows: 5 by default (at most half the stages); the environment variable
+// STMG_VANKA_WS overrides it (0: one-shot k_vanka_apply blocks, kept for comparisons; read once).
+inline int vanka_ws_groups() {
+  static const int c = [] {
+    const char* v = std::getenv("STMG_VANKA_WS");
+    if (!v) return 5;
+    const int x = std::atoi(v);
+    return x < 0 ? 0 : (x > 8 ? 8 : x);
+  }();
+  return c;
+}
+inline bool vanka_ws_enabled() { return vanka_ws_groups() > 0; }
 
 // The stored inverse blob of a cell fits shared memory (else k_vanka_apply_global).
 static bool apply_onchip(const Level& lv, size_t es_store, size_t es) {
@@ -177,6 +193,7 @@ static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv
                                unsigned extra_tx, cudaStream_t s, int slots, SlotStrides zs) {
   // one block per cell, threads = spatial patch rows rounded up to whole warps
   const int ms = (int)vanka_spatial_size(lv), kp1 = lv.k + 1;
+  if (ms != patch_rows<D, N>()) return cudaErrorInvalidValue;
   const int threads = ((ms + 31) / 32) * 32;
   if (!apply_onchip(lv, sizeof(SI), sizeof(T))) {
     const int mr = (ms + 1) & ~1;
@@ -185,6 +202,38 @@ static cudaError_t apply_cells(const Level& lv, const Problem& pb, const SI* inv
         level_args<T>(lv, pb, 0.0), inv, scale, res, d, (T)omega, (T)omega_p, kp1, lv.npc,
         make_teig<T>(lv.tabs, pb.tau), ci, zs);
     return cudaSuccess;
+  }
+  // 2D patches of more than one warp's rows: the warp-specialised persistent kernel, one block
+  // per SM, as many stages as fit 200 KB of shared memory
+  if constexpr (D == 2) {
+    if (threads > 32 && vanka_ws_enabled()) {
+      const size_t blob = apply_blob_bytes(kp1, ms, sizeof(SI));
+      const size_t rtb = ws_rt_bytes(kp1, ms, sizeof(T));
+      const int cw = vanka_ws_groups();
+      int S = (int)((200 * 1024 - cw * rtb - 16) / (blob + 16));
+      if (S > 16) S = 16;
+      int C = S >= 2 * cw ? cw : S / 2;
+      // the block's registers must fit the SM's 64 K
+      cudaFuncAttributes fa{};
+      cudaError_t e = cudaFuncGetAttributes(&fa, k_vanka_apply_ws<T, SI, D, N>);
+      if (e != cudaSuccess) return e;
+      const int regs = (fa.numRegs + 7) & ~7;        // allocation granularity
+      while (C > 1 && ((32 + C * threads) * regs > 65536 || 32 + C * threads > fa.maxThreadsPerBlock)) --C;
+      if (C >= 1 && (32 + C * threads) * regs <= 65536 && 32 + C * threads <= fa.maxThreadsPerBlock) {
+        const size_t wsm = ws_smem_bytes(kp1, ms, sizeof(SI), sizeof(T), S, C);
+        e = allow_smem(k_vanka_apply_ws<T, SI, D, N>, wsm);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        const unsigned grid = (unsigned)(ci.count < sms ? ci.count : sms);
+        k_vanka_apply_ws<T, SI, D, N><<<dim3(grid, slots), 32 + C * threads, wsm, s>>>(
+            level_args<T>(lv, pb, 0.0), inv, scale, res, d, (T)omega, (T)omega_p, kp1, lv.npc,
+            make_teig<T>(lv.tabs, pb.tau), ci, wstat, extra_tx, zs, S, C, threads);
+        return cudaSuccess;
+      }
+    }
   }
   // cells per block: 4 for one-warp patches (32 resident blocks per SM), else 1
   const size_t slot = apply_slot_bytes(kp1, ms, sizeof(SI), sizeof(T));
