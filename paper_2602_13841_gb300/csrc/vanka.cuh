@@ -299,6 +299,7 @@ __global__ void k_elem_global(VankaArgs<T> V, Tab<T> tb, int64_t c0, int64_t c1)
 }
 
 // ---------------------------------------------------------------------------- Gauss-Jordan
+constexpr int kGjBatch = 8;                        // rows loaded ahead in an elimination pass
 // In-place inverse of the m x m row-major matrix S (leading dimension ld) with partial (row)
 // pivoting; column interchanges undo the row interchanges at the end.  All threads of the
 // block take part; returns false (block-uniformly) on a zero pivot.
@@ -337,14 +338,27 @@ __device__ bool gauss_jordan(T* S, int m, int ld, int* piv_row, T* colbuf) {
     __syncthreads();
     for (int i = tid; i < m; i += nt) if (i != p) S[i * ld + p] = 0;
     __syncthreads();
-    // elimination: thread owns column j and every `rs`-th row (no division in the loop)
+    // elimination: thread owns column j and every `rs`-th row (no division in the loop); rows
+    // in batches of kGjBatch loads before their stores, so that a matrix in global memory is
+    // not updated one dependent round trip at a time
     if (nt >= m) {
       const int rs = nt / m;
       if (tid < rs * m) {
         const int j = tid % m, chunk = tid / m;
         const T prow = S[p * ld + j];
-        for (int i = chunk; i < m; i += rs)
-          if (i != p) S[i * ld + j] -= colbuf[i] * prow;
+        for (int i0 = chunk; i0 < m; i0 += kGjBatch * rs) {
+          T v[kGjBatch];
+#pragma unroll
+          for (int u = 0; u < kGjBatch; ++u) {
+            const int i = i0 + u * rs;
+            v[u] = i < m ? S[i * ld + j] : (T)0;
+          }
+#pragma unroll
+          for (int u = 0; u < kGjBatch; ++u) {
+            const int i = i0 + u * rs;
+            if (i < m && i != p) S[i * ld + j] = v[u] - colbuf[i] * prow;
+          }
+        }
       }
     } else {
       for (int j = tid; j < m; j += nt) {
@@ -418,11 +432,23 @@ __device__ bool gauss_jordan_c(T* Sr, T* Si, int m, int* piv_row, T* cr, T* ci) 
       if (tid < rs * m) {
         const int j = tid % m, chunk = tid / m;
         const T br = Sr[p * m + j], bim = Si[p * m + j];
-        for (int i = chunk; i < m; i += rs)
-          if (i != p) {
-            Sr[i * m + j] -= cr[i] * br - ci[i] * bim;
-            Si[i * m + j] -= cr[i] * bim + ci[i] * br;
+        for (int i0 = chunk; i0 < m; i0 += kGjBatch * rs) {
+          T vr[kGjBatch], vi[kGjBatch];
+#pragma unroll
+          for (int u = 0; u < kGjBatch; ++u) {
+            const int i = i0 + u * rs;
+            vr[u] = i < m ? Sr[i * m + j] : (T)0;
+            vi[u] = i < m ? Si[i * m + j] : (T)0;
           }
+#pragma unroll
+          for (int u = 0; u < kGjBatch; ++u) {
+            const int i = i0 + u * rs;
+            if (i < m && i != p) {
+              Sr[i * m + j] = vr[u] - (cr[i] * br - ci[i] * bim);
+              Si[i * m + j] = vi[u] - (cr[i] * bim + ci[i] * br);
+            }
+          }
+        }
       }
     } else {
       for (int j = tid; j < m; j += nt) {
@@ -592,7 +618,7 @@ __global__ void k_patch(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t c0, int64
 // (V.work, V.wslot entries per slot; the slots together stay L2-resident); blocks stride over
 // the cells.  Only the pivot bookkeeping is in shared memory.
 template <typename T, int D, int N>
-__global__ void k_patch_global(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t c0, int64_t c1) {
+__global__ void __launch_bounds__(512, 2) k_patch_global(VankaArgs<T> V, Tab<T> tb, TEig<T> te, int64_t c0, int64_t c1) {
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
   const int ms = MV + tb.npc;
