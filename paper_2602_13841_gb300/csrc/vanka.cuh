@@ -857,8 +857,66 @@ __global__ void k_vanka_apply(LevelArgs<T> L, const SI* __restrict__ inv, const 
 // ahead is still current when its cell is solved.  The products are those of k_vanka_apply, in
 // the same order.
 // Shared memory: [S stages | C rt buffers (kp1 x mr T) | full[S] | empty[S] | abort flag].
+// rt rows of the persistent kernel are padded to a multiple of 4 entries, so that every unit row
+// starts on a 16-byte boundary and is read four entries at a time.
+__host__ __device__ inline int ws_rt_row(int ms) { return (ms + 3) & ~3; }
 __host__ __device__ inline size_t ws_rt_bytes(int kp1, int ms, size_t t) {
-  return ((size_t)kp1 * ((ms + 1) & ~1) * t + 15) & ~(size_t)15;
+  return ((size_t)kp1 * ws_rt_row(ms) * t + 15) & ~(size_t)15;
+}
+
+// Row i of the product of a stored inverse block with the vector r (real block) or with r0 + i r1
+// (complex block, entries interleaved re/im), over the patch rows j = 0 .. MS - 1 in order; r, r0
+// and r1 are 16-byte aligned shared-memory rows read as vectors of 16 bytes (4 floats / 2 doubles).
+template <typename T, typename SI, int MS>
+__device__ __forceinline__ T row_product_re(const SI* blk, int st, int i, const T* r) {
+  constexpr int W = 16 / sizeof(T);
+  T ar = 0;
+#pragma unroll
+  for (int j0 = 0; j0 < MS; j0 += W) {
+    T x[W];
+    if constexpr (W == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(r + j0);
+      x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else {
+      const double2 v = *reinterpret_cast<const double2*>(r + j0);
+      x[0] = v.x; x[1] = v.y;
+    }
+#pragma unroll
+    for (int u = 0; u < W; ++u)
+      if (j0 + u < MS) ar += (T)InvLd<SI>::re(blk + (j0 + u) * st + i) * x[u];
+  }
+  return ar;
+}
+template <typename T, typename SI, int MS>
+__device__ __forceinline__ void row_product_cx(const SI* blk, int st, int i, const T* r0, const T* r1, T* ar_out,
+                                               T* ai_out) {
+  constexpr int W = 16 / sizeof(T);
+  T ar = 0, ai = 0;
+#pragma unroll
+  for (int j0 = 0; j0 < MS; j0 += W) {
+    T xr[W], xi[W];
+    if constexpr (W == 4) {
+      const float4 a = *reinterpret_cast<const float4*>(r0 + j0);
+      const float4 b = *reinterpret_cast<const float4*>(r1 + j0);
+      xr[0] = a.x; xr[1] = a.y; xr[2] = a.z; xr[3] = a.w;
+      xi[0] = b.x; xi[1] = b.y; xi[2] = b.z; xi[3] = b.w;
+    } else {
+      const double2 a = *reinterpret_cast<const double2*>(r0 + j0);
+      const double2 b = *reinterpret_cast<const double2*>(r1 + j0);
+      xr[0] = a.x; xr[1] = a.y;
+      xi[0] = b.x; xi[1] = b.y;
+    }
+#pragma unroll
+    for (int u = 0; u < W; ++u)
+      if (j0 + u < MS) {
+        const auto v = InvLd<SI>::cx(blk + 2 * ((j0 + u) * st + i));
+        const T vr = (T)v.x, vi = (T)v.y;
+        ar += vr * xr[u] - vi * xi[u];
+        ai += vr * xi[u] + vi * xr[u];
+      }
+  }
+  *ar_out = ar;
+  *ai_out = ai;
 }
 __host__ __device__ inline size_t ws_smem_bytes(int kp1, int ms, size_t si, size_t t, int S, int C) {
   return (size_t)S * apply_blob_bytes(kp1, ms, si) + (size_t)C * ws_rt_bytes(kp1, ms, t) + (size_t)2 * S * 8 + 16;
@@ -904,7 +962,7 @@ __global__ void k_vanka_apply_ws(LevelArgs<T> L, const SI* __restrict__ inv, con
   d += blockIdx.y * zs.vec;
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
-  const int ms = MV + npc, st = inv_stride(ms, (int)sizeof(SI)), mr = (ms + 1) & ~1;
+  const int ms = MV + npc, st = inv_stride(ms, (int)sizeof(SI)), mr = ws_rt_row(ms);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const size_t blob = apply_blob_bytes(kp1, ms, sizeof(SI));
   const size_t rtb = ws_rt_bytes(kp1, ms, sizeof(T));
@@ -1012,19 +1070,8 @@ __global__ void k_vanka_apply_ws(LevelArgs<T> L, const SI* __restrict__ inv, con
           const SI* blk = sinv + (int64_t)te.off[e] * ms * st;
           const T* r0 = rt + te.off[e] * mr;
           T ar = 0, ai = 0;
-          if (!te.cplx[e]) {
-#pragma unroll
-            for (int j = 0; j < patch_rows<D, N>(); ++j) ar += (T)InvLd<SI>::re(blk + j * st + i) * r0[j];
-          } else {
-            const T* r1 = r0 + mr;
-#pragma unroll
-            for (int j = 0; j < patch_rows<D, N>(); ++j) {
-              const auto v = InvLd<SI>::cx(blk + 2 * (j * st + i));
-              const T vr = (T)v.x, vi = (T)v.y, xr = r0[j], xi = r1[j];
-              ar += vr * xr - vi * xi;
-              ai += vr * xi + vi * xr;
-            }
-          }
+          if (!te.cplx[e]) ar = row_product_re<T, SI, patch_rows<D, N>()>(blk, st, i, r0);
+          else row_product_cx<T, SI, patch_rows<D, N>()>(blk, st, i, r0, r0 + mr, &ar, &ai);
           const T sc = scale ? (T)scale[ccur * te.nblk + e] : (T)1;
 #pragma unroll
           for (int q = 0; q < MAXKP1; ++q)
