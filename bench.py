@@ -678,14 +678,15 @@ def _peaks():
 # warp instructions, i.e. 32 (2 x 16.80 + 6.08) M = 1.270 GFLOP, of which the tile's halo
 # recompute is 22 % (16 x 8 cells computed per 15 x 7 owned): 1.270e9 / 1.219 / (3 x 65536).
 FP32_APPLY_FLOPS_PER_CELL_NODE = 1.270e9 / (128.0 / 105.0) / (3 * 65536)
-# FP32 FMA peak of one GB300: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz / 1e12 (about 120 FFMA per
-# SM per clock sustained in a dependent-chain probe, 73.4 TFLOP/s).
+# FP32 FMA peak of one GB300 as measured on this hardware: about 120 FFMA per SM per clock in a
+# dependent-chain probe, x 2 FLOP x 152 SMs x 2.07 GHz = 73.4 TFLOP/s (the nominal 128 lanes per SM
+# give 80.5).
 FP32_PEAK_TFLOPS = 73.4
 
 # DRAM bytes (read + write) per cell of the finest-level Vanka apply (k_vanka_apply_ws), FP32
 # inverses, Q3/P2/DG(2): ncu capture of one colour launch on the 128^2 mesh of the same recipe,
-# 78.69 MB for 4096 cells; scaled to a 256^2 launch by its cells.
-VANKA_DRAM_BYTES_PER_CELL = 78.690304e6 / 4096
+# 78.70 MB for 4096 cells; scaled to a 256^2 launch by its cells.
+VANKA_DRAM_BYTES_PER_CELL = 78.702848e6 / 4096
 
 
 def _inverse_gb(w, args):

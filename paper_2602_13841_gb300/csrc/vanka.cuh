@@ -44,7 +44,7 @@ struct VankaArgs {
 // Column stride of a stored patch inverse: the smallest st >= m for which one m x st block of
 // `es`-byte entries is a whole number of 16-byte units, so that every block and every cell's blob
 // starts 16-byte aligned (the bulk copy's requirement) with the least padding (FP32, m = 38: 38).
-__host__ __device__ inline int inv_stride(int m, int es) {
+__host__ __device__ constexpr inline int inv_stride(int m, int es) {
   int st = m;
   while (((long long)m * st * es) % 16 != 0) ++st;
   return st;
@@ -868,8 +868,9 @@ __host__ __device__ inline size_t ws_rt_bytes(int kp1, int ms, size_t t) {
 // (complex block, entries interleaved re/im), over the patch rows j = 0 .. MS - 1 in order; r, r0
 // and r1 are 16-byte aligned shared-memory rows read as vectors of 16 bytes (4 floats / 2 doubles).
 template <typename T, typename SI, int MS>
-__device__ __forceinline__ T row_product_re(const SI* blk, int st, int i, const T* r) {
+__device__ __forceinline__ T row_product_re(const SI* blk, int i, const T* r) {
   constexpr int W = 16 / sizeof(T);
+  constexpr int st = inv_stride(MS, (int)sizeof(SI));   // compile time: immediate load offsets
   T ar = 0;
 #pragma unroll
   for (int j0 = 0; j0 < MS; j0 += W) {
@@ -888,9 +889,10 @@ __device__ __forceinline__ T row_product_re(const SI* blk, int st, int i, const 
   return ar;
 }
 template <typename T, typename SI, int MS>
-__device__ __forceinline__ void row_product_cx(const SI* blk, int st, int i, const T* r0, const T* r1, T* ar_out,
+__device__ __forceinline__ void row_product_cx(const SI* blk, int i, const T* r0, const T* r1, T* ar_out,
                                                T* ai_out) {
   constexpr int W = 16 / sizeof(T);
+  constexpr int st = inv_stride(MS, (int)sizeof(SI));
   T ar = 0, ai = 0;
 #pragma unroll
   for (int j0 = 0; j0 < MS; j0 += W) {
@@ -1070,8 +1072,8 @@ __global__ void k_vanka_apply_ws(LevelArgs<T> L, const SI* __restrict__ inv, con
           const SI* blk = sinv + (int64_t)te.off[e] * ms * st;
           const T* r0 = rt + te.off[e] * mr;
           T ar = 0, ai = 0;
-          if (!te.cplx[e]) ar = row_product_re<T, SI, patch_rows<D, N>()>(blk, st, i, r0);
-          else row_product_cx<T, SI, patch_rows<D, N>()>(blk, st, i, r0, r0 + mr, &ar, &ai);
+          if (!te.cplx[e]) ar = row_product_re<T, SI, patch_rows<D, N>()>(blk, i, r0);
+          else row_product_cx<T, SI, patch_rows<D, N>()>(blk, i, r0, r0 + mr, &ar, &ai);
           const T sc = scale ? (T)scale[ccur * te.nblk + e] : (T)1;
 #pragma unroll
           for (int q = 0; q < MAXKP1; ++q)
