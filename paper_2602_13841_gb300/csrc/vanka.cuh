@@ -475,6 +475,39 @@ __device__ bool gauss_jordan_c(T* Sr, T* Si, int m, int* piv_row, T* cr, T* ci) 
 }
 
 // ---------------------------------------------------------------------------- patch build
+// The cells K' around the cell at cc (offsets o in {-1, 0, 1}^D) that contain both nodes i and j
+// of the cell (multi-indices im, jm within it), visited in the order of the offset code
+// nb = (o0 + 1) + 3 (o1 + 1) + 9 (o2 + 1): f(nc, ii, jj) gets K''s linear index and the two nodes'
+// local indices in K'.  Per dimension at most two offsets qualify (0, and -1 or +1 when both
+// nodes lie on that side), so a patch entry visits 1 to 2^D cells instead of testing 3^D.
+template <int D, int N, typename F>
+__device__ __forceinline__ void for_shared_cells(const int* cc, int n, const int* im, const int* jm, F&& f) {
+  int off[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  int cnt[3] = {1, 1, 1};
+  for (int l = 0; l < D; ++l) {
+    cnt[l] = 0;
+    for (int o = -1; o <= 1; ++o) {
+      const int x = cc[l] + o, a = im[l] - o * (N - 1), b = jm[l] - o * (N - 1);
+      if (x >= 0 && x < n && a >= 0 && a < N && b >= 0 && b < N) off[l][cnt[l]++] = o;
+    }
+  }
+  for (int u2 = 0; u2 < cnt[2]; ++u2)
+    for (int u1 = 0; u1 < cnt[1]; ++u1)
+      for (int u0 = 0; u0 < cnt[0]; ++u0) {
+        const int o[3] = {off[0][u0], off[1][u1], off[2][u2]};
+        int64_t nc = 0, s = 1;
+        int ii = 0, jj = 0, si = 1;
+        for (int l = 0; l < D; ++l) {
+          nc += (int64_t)(cc[l] + o[l]) * s;
+          s *= n;
+          ii += (im[l] - o[l] * (N - 1)) * si;
+          jj += (jm[l] - o[l] * (N - 1)) * si;
+          si *= N;
+        }
+        f(nc, ii, jj);
+      }
+}
+
 // Spatial patch ordering: velocity (c, i) -> c*NL + i, then pressure mode m -> MV + m.  The
 // surrogate patch matrix of Eq. vanka0 is, time node by time node,
 //   S~ = [ K^tau (x) M + W (x) A ,  W (x) B^T ;  W (x) B , 0 ],   W = diag(w_a),
@@ -493,7 +526,6 @@ __device__ bool patch_cell(const VankaArgs<T>& V, const Tab<T>& tb, const TEig<T
   int cc[3] = {0, 0, 0};
   cell_coords<D>(cell, L.n, cc);
   const int tid = threadIdx.x, nt = blockDim.x;
-  constexpr int NNB = (D == 2) ? 9 : 27;
   // assembled velocity and mass blocks: sum over neighbours K' sharing both nodes
   for (int ent = tid; ent < MV * MV; ent += nt) {
     const int row = ent / MV, col = ent % MV;
@@ -501,20 +533,9 @@ __device__ bool patch_cell(const VankaArgs<T>& V, const Tab<T>& tb, const TEig<T
     int im[3], jm[3];
     node_multi<D, N>(i, im); node_multi<D, N>(j, jm);
     T acc = 0;
-    for (int nb = 0; nb < NNB; ++nb) {
-      int o[3] = {nb % 3 - 1, (nb / 3) % 3 - 1, nb / 9 - 1};
-      bool ok = true;
-      int64_t nc = 0, s = 1;
-      int ii = 0, jj = 0, si = 1;
-      for (int l = 0; l < D; ++l) {
-        int x = cc[l] + o[l];
-        int a = im[l] - o[l] * (N - 1), b = jm[l] - o[l] * (N - 1);
-        if (x < 0 || x >= L.n || a < 0 || a >= N || b < 0 || b >= N) { ok = false; break; }
-        nc += (int64_t)x * s; s *= L.n;
-        ii += a * si; jj += b * si; si *= N;
-      }
-      if (ok) acc += V.EA[(nc - V.ebase) * (int64_t)MV * MV + (int64_t)(c * NL + ii) * MV + e * NL + jj];
-    }
+    for_shared_cells<D, N>(cc, L.n, im, jm, [&](int64_t nc, int ii, int jj) {
+      acc += V.EA[(nc - V.ebase) * (int64_t)MV * MV + (int64_t)(c * NL + ii) * MV + e * NL + jj];
+    });
     Ap[ent] = acc;
   }
   for (int ent = tid; ent < NL * NL; ent += nt) {
@@ -522,20 +543,9 @@ __device__ bool patch_cell(const VankaArgs<T>& V, const Tab<T>& tb, const TEig<T
     int im[3], jm[3];
     node_multi<D, N>(i, im); node_multi<D, N>(j, jm);
     T acc = 0;
-    for (int nb = 0; nb < NNB; ++nb) {
-      int o[3] = {nb % 3 - 1, (nb / 3) % 3 - 1, nb / 9 - 1};
-      bool ok = true;
-      int64_t nc = 0, s = 1;
-      int ii = 0, jj = 0, si = 1;
-      for (int l = 0; l < D; ++l) {
-        int x = cc[l] + o[l];
-        int a = im[l] - o[l] * (N - 1), b = jm[l] - o[l] * (N - 1);
-        if (x < 0 || x >= L.n || a < 0 || a >= N || b < 0 || b >= N) { ok = false; break; }
-        nc += (int64_t)x * s; s *= L.n;
-        ii += a * si; jj += b * si; si *= N;
-      }
-      if (ok) acc += V.EM[(nc - V.ebase) * (int64_t)NL * NL + (int64_t)ii * NL + jj];
-    }
+    for_shared_cells<D, N>(cc, L.n, im, jm, [&](int64_t nc, int ii, int jj) {
+      acc += V.EM[(nc - V.ebase) * (int64_t)NL * NL + (int64_t)ii * NL + jj];
+    });
     Mp[ent] = acc;
   }
   __syncthreads();

@@ -27,7 +27,6 @@ template <typename T, int D, int N>
 __global__ void k_patch_exact(VankaArgs<T> V, Tab<T> tb, int64_t ea_tstride, int64_t c0, int64_t c1) {
   constexpr int NL = Shape<D, N>::Q;
   constexpr int MV = D * NL;
-  constexpr int NNB = (D == 2) ? 9 : 27;
   const int npc = tb.npc, kp1 = tb.k + 1, ms = MV + npc, mst = kp1 * ms;
   const int st = inv_stride(mst, (int)sizeof(T));
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -42,32 +41,16 @@ __global__ void k_patch_exact(VankaArgs<T> V, Tab<T> tb, int64_t ea_tstride, int
   int cc[3] = {0, 0, 0};
   cell_coords<D>(cell, L.n, cc);
   const int tid = threadIdx.x, nt = blockDim.x;
-  // neighbour sum of the entry (i, j) of the element blocks sharing both nodes: returns the
-  // element-block offset of neighbour nb's (ii, jj) entry or -1
-  auto nbr = [&](int nb, int i, int j, int* ii, int* jj) -> int64_t {
-    const int o[3] = {nb % 3 - 1, (nb / 3) % 3 - 1, nb / 9 - 1};
+  // neighbour sums over the cells sharing both nodes of an entry (for_shared_cells)
+  for (int ent = tid; ent < NL * NL; ent += nt) {
+    const int i = ent / NL, j = ent % NL;
     int im[3], jm[3];
     node_multi<D, N>(i, im);
     node_multi<D, N>(j, jm);
-    int64_t nc = 0, s = 1;
-    int a_ = 0, b_ = 0, si = 1;
-    for (int l = 0; l < D; ++l) {
-      const int x = cc[l] + o[l], a = im[l] - o[l] * (N - 1), b = jm[l] - o[l] * (N - 1);
-      if (x < 0 || x >= L.n || a < 0 || a >= N || b < 0 || b >= N) return -1;
-      nc += (int64_t)x * s; s *= L.n;
-      a_ += a * si; b_ += b * si; si *= N;
-    }
-    *ii = a_; *jj = b_;
-    return nc - V.ebase;
-  };
-  for (int ent = tid; ent < NL * NL; ent += nt) {
-    const int i = ent / NL, j = ent % NL;
     T acc = 0;
-    for (int nb = 0; nb < NNB; ++nb) {
-      int ii, jj;
-      const int64_t ec = nbr(nb, i, j, &ii, &jj);
-      if (ec >= 0) acc += V.EM[ec * (int64_t)NL * NL + (int64_t)ii * NL + jj];
-    }
+    for_shared_cells<D, N>(cc, L.n, im, jm, [&](int64_t nc, int ii, int jj) {
+      acc += V.EM[(nc - V.ebase) * (int64_t)NL * NL + (int64_t)ii * NL + jj];
+    });
     Mp[ent] = acc;
   }
   __syncthreads();
@@ -93,12 +76,13 @@ __global__ void k_patch_exact(VankaArgs<T> V, Tab<T> tb, int64_t ea_tstride, int
     for (int ent = tid; ent < MV * MV; ent += nt) {
       const int row = ent / MV, cl = ent % MV;
       const int c = row / NL, i = row % NL, e = cl / NL, j = cl % NL;
+      int im[3], jm[3];
+      node_multi<D, N>(i, im);
+      node_multi<D, N>(j, jm);
       T acc = 0;
-      for (int nb = 0; nb < NNB; ++nb) {
-        int ii, jj;
-        const int64_t ec = nbr(nb, i, j, &ii, &jj);
-        if (ec >= 0) acc += EA[ec * (int64_t)MV * MV + (int64_t)(c * NL + ii) * MV + e * NL + jj];
-      }
+      for_shared_cells<D, N>(cc, L.n, im, jm, [&](int64_t nc, int ii, int jj) {
+        acc += EA[(nc - V.ebase) * (int64_t)MV * MV + (int64_t)(c * NL + ii) * MV + e * NL + jj];
+      });
       S[(a * ms + row) * mst + a * ms + cl] += tb.w[a] * acc;
     }
     __syncthreads();
