@@ -58,3 +58,33 @@ def test_footprint_follows_the_hierarchy_option():
     assert fp(k=2, keep_time_degree=1) > fp(k=2, keep_time_degree=0)
     assert fp(k=1, keep_time_degree=1) == fp(k=1, keep_time_degree=0)
     assert fp(k=2, problem="CAV3D", dim=3, n_cells_1d=8) > 0
+
+
+def _c_layout(tmp_path, ctype, fields):
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "stmg.h"', "int main(void) {",
+             '  printf("%%zu\\n", sizeof(%s));' % ctype]
+    lines += ['  printf("%%zu\\n", offsetof(%s, %s));' % (ctype, f) for f in fields]
+    lines += ["  return 0;", "}"]
+    src = tmp_path / (ctype + ".c")
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / ctype
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    return [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+
+
+@pytest.mark.parametrize("ctype,pyname", [("stmg_params", "Params"), ("stmg_stats", "Stats")])
+def test_struct_layout_matches_the_header(tmp_path, ctype, pyname):
+    """The ctypes mirrors of the ABI structs have the C structs' sizes and field offsets (compiled
+    with the host C compiler from include/stmg.h)."""
+    from paper_2602_13841_gb300 import stmg
+    cls = getattr(stmg, pyname)
+    fields = [f for f, _ in cls._fields_]
+    out = _c_layout(tmp_path, ctype, fields)
+    assert out[0] == ctypes.sizeof(cls)
+    for f, off in zip(fields, out[1:]):
+        assert getattr(cls, f).offset == off, f
