@@ -222,3 +222,30 @@ def test_midpoint_surrogate_error_is_first_order_in_tau():
         assert lhs <= np.linalg.norm(np.linalg.inv(S), 2) * nE * (1 + 1e-12)
     rates = [ratios[i] / ratios[i + 1] for i in range(len(ratios) - 1)]
     assert all(1.8 < q < 2.2 for q in rates[1:]), (ratios, rates)
+
+
+def test_two_grid_diverges_for_an_unresolved_convective_flow():
+    """A limit of the method as read, recorded in the design notes: on 2D 32^2 Q2/P1 DG(0) at
+    Re 1623 (dt = 0.05) the two-grid error propagation I - B^{-1} J (one h-level, one sweep) grows
+    for the Taylor-Green state while it contracts for the manufactured solution at the same Re
+    and mesh.  Power iteration from a seeded vector, mean-zero pressure kept."""
+    from oracle import krylov, problems
+    out = {}
+    for pname in ("TG2D", "MMS2D"):
+        prob = problems.make(pname, 1.0 / 1623.0)
+        S = krylov.SlabSolver(2, 32, 1, 0, inputs.vertices(2, 32, 0.1, 1), 0.05, prob, max_h=1)
+        L = S.L
+        V = forms.interpolate_velocity(L.space, prob.v0)
+        U = np.concatenate([V, np.zeros(L.lay.Np)])
+        S.mg.setup(U)
+        J = forms.jacobian(L.space, L.td, U, prob.nu)
+        e = S.project(np.random.default_rng(0).standard_normal(L.Nst))
+        e /= np.linalg.norm(e)
+        growth = []
+        for _ in range(12):
+            e = S.project(e - S.mg.vcycle(J @ e))
+            growth.append(np.linalg.norm(e))
+            e /= growth[-1]
+        out[pname] = float(np.exp(np.mean(np.log(growth[-5:]))))
+    assert out["TG2D"] > 2.0, out
+    assert out["MMS2D"] < 0.7, out
