@@ -249,3 +249,83 @@ def test_two_grid_diverges_for_an_unresolved_convective_flow():
         out[pname] = float(np.exp(np.mean(np.log(growth[-5:]))))
     assert out["TG2D"] > 2.0, out
     assert out["MMS2D"] < 0.7, out
+
+
+def test_time_p_coarsening_amplifies_smooth_errors_in_the_dropped_temporal_mode():
+    """The mechanism behind the FGMRES counts of the paper's coarsening order (the design notes'
+    reading on time p-coarsening): on 2D 8^2 Q3/P2 DG(2) (Taylor-Green state, Re 100, tau = h) an
+    error that is smooth in space and lies in the temporal mode that DG(2) -> DG(1) drops (the
+    Legendre polynomial of degree 2 at the Radau nodes) grows in the first V-cycle when the time
+    degree is coarsened, and contracts when DG(2) is kept on every level; errors in the lowest
+    temporal mode contract with both hierarchies."""
+    from numpy.polynomial import legendre as npleg
+    from oracle import problems
+    from oracle.reference import radau_right
+    d, n, r, k, nu = 2, 8, 2, 2, 1e-2
+    first = {}
+    for keep in (False, True):
+        mg = multigrid.Multigrid(d, n, r, k, inputs.vertices(d, n, 0.0, 1), 1.0 / n, nu, keep_k=keep)
+        L = mg.levels[0]
+        prob = problems.make("TG2D", nu)
+        V = forms.interpolate_velocity(L.space, prob.v0)
+        U = np.concatenate([np.tile(V, k + 1), np.zeros((k + 1) * L.lay.Np)])
+        mg.setup(U)
+        J = mg.J[0]
+        X = L.space.node_coords()
+        smooth = np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1])
+        that, _ = radau_right(k)
+        for deg in (0, k):
+            q = npleg.legval(that, [0] * deg + [1])
+            e = np.zeros(L.Nst)
+            for a in range(k + 1):
+                e[a * L.lay.Nv:a * L.lay.Nv + d * len(smooth)] = q[a] * np.tile(smooth, d)
+            first[(keep, deg)] = np.linalg.norm(e - mg.vcycle(J @ e)) / np.linalg.norm(e)
+    assert first[(False, k)] > 1.5, first          # paper's order: amplified
+    assert first[(True, k)] < 0.5, first           # DG(2) kept: contracted
+    assert first[(False, 0)] < 0.5 and first[(True, 0)] < 0.5, first
+
+
+def _slowest_mode(keep_k, nu_tc=0, d=2, n=8, r=1, k=2, nu=1e-2):
+    """Power iteration on the V-cycle error propagation I - B^{-1} J with the constant pressure of
+    every time node projected out: the geometric-mean growth of the last 20 of 60 steps, the
+    pressure share of the limiting vector, and the shares of its pressure in the temporal Legendre
+    modes of degree 0 .. k."""
+    from numpy.polynomial import legendre as npleg
+    from oracle import krylov, problems
+    from oracle.reference import radau_right
+    prob = problems.make("TG2D", nu)
+    S = krylov.SlabSolver(d, n, r, k, inputs.vertices(d, n, 0.0, 1), 1.0 / n, prob, keep_k=keep_k, nu_tc=nu_tc)
+    L, mg = S.L, S.mg
+    V = forms.interpolate_velocity(L.space, prob.v0)
+    U = np.concatenate([np.tile(V, k + 1), np.zeros((k + 1) * L.lay.Np)])
+    mg.setup(U)
+    J = mg.J[0]
+    e = S.project(np.random.default_rng(0).standard_normal(L.Nst))
+    e /= np.linalg.norm(e)
+    growth = []
+    for _ in range(60):
+        e = S.project(e - mg.vcycle(J @ e))
+        growth.append(np.linalg.norm(e))
+        e /= growth[-1]
+    nv, npr = L.lay.Nv, L.lay.Np
+    that, _ = radau_right(k)
+    Q = np.stack([npleg.legval(that, [0] * g + [1]) for g in range(k + 1)])
+    pres = np.stack([e[(k + 1) * nv + a * npr:(k + 1) * nv + (a + 1) * npr] for a in range(k + 1)])
+    modal = np.sum((np.linalg.inv(Q.T) @ pres) ** 2, axis=1)
+    return (float(np.exp(np.mean(np.log(growth[-20:])))), float(np.linalg.norm(e[(k + 1) * nv:]) ** 2),
+            modal / modal.sum())
+
+
+def test_time_p_coarsening_leaves_smooth_pressure_errors_in_the_dropped_temporal_mode():
+    """The cause of the FGMRES counts of the paper's coarsening order (the design notes' reading
+    on time p-coarsening), on 2D 8^2 Q2/P1 DG(2) (Taylor-Green state, Re 100, tau = h): with
+    DG(2) -> DG(1) the slowest error of the V-cycle is a pressure error, mostly in the temporal
+    mode that DG(1) cannot represent, and it contracts by only about 0.96 per cycle; extra sweeps
+    on the DG(2) level help a little; with DG(2) kept on every level the slowest error contracts
+    by about 0.56."""
+    rate, pshare, modal = _slowest_mode(False)
+    assert rate > 0.93 and pshare > 0.95 and modal[2] > 0.5, (rate, pshare, modal)
+    rate5 = _slowest_mode(False, nu_tc=5)[0]
+    assert rate5 < rate - 0.03, (rate5, rate)
+    rate_keep = _slowest_mode(True)[0]
+    assert rate_keep < 0.65, rate_keep
